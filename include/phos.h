@@ -1,0 +1,331 @@
+/*
+ * phos.h -- C ABI of the PhOS data plane on B300 (sm_103a).
+ *
+ * The data plane of concurrent GPU checkpoint/restore with validated
+ * speculation (PhoenixOS, SOSP'25, arXiv 2405.12079):
+ *   - argument-based speculation of a kernel's read/write buffers (Sec. 4.1,
+ *     read set in Sec. 6), host side;
+ *   - access validation of recorded load/store addresses against the
+ *     speculated buffers (Sec. 4.1 "Runtime validation"), CUDA;
+ *   - the copy engine behind soft copy-on-write (Sec. 4.2), soft recopy
+ *     (Sec. 4.3, chunked per Sec. 5) and soft on-demand restore (Sec. 6),
+ *     CUDA;
+ *   - the protocol state machines that drive them (phos_ckpt_*,
+ *     phos_restore_*), host C++.
+ *
+ * Conventions for every call
+ *   - Return value: PHOS_OK or one of the error codes below; the message of
+ *     the last failure on the calling thread is phos_last_error().
+ *   - Device work is asynchronous on the caller's stream (a cudaStream_t
+ *     passed as phos_stream_t; NULL = legacy default stream).  Errors found
+ *     on the device are written to a caller-owned uint32_t status word
+ *     (d_status, device or mapped memory, zeroed once by the caller): the
+ *     first error code sticks, later calls never clear it.  Read it after
+ *     synchronising the stream.
+ *   - Ownership: the caller owns every buffer passed in (live memory,
+ *     staging, image, traces, outputs); the library never frees caller
+ *     memory and never synchronises, except where a call says so.  The
+ *     library owns only its opaque handles and their scratch memory.
+ *   - "image" pointers may be pinned host memory (cudaHostAlloc or
+ *     cudaHostRegister; the kernels reach it through its mapped device
+ *     address) or device memory; pageable host memory is rejected.
+ *   - Calls that use the same table handle and run concurrently on
+ *     different streams race on the handle's scratch; order them.
+ */
+#ifndef PHOS_H
+#define PHOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t phos_status;
+enum {
+    PHOS_OK = 0,
+    PHOS_EINVAL = 1,     /* bad argument, table, descriptor or record      */
+    PHOS_ENOMEM = 2,     /* library scratch allocation failed              */
+    PHOS_EBUDGET = 3,    /* staging budget exhausted and no fallback       */
+    PHOS_ECUDA = 4,      /* a CUDA runtime call failed                     */
+    PHOS_ETIMEDOUT = 5,  /* a bounded device-side wait gave up             */
+    PHOS_ECORRUPT = 6,   /* digest mismatch in a checkpoint image          */
+    PHOS_EMISSPEC = 7    /* validation found a mis-speculation that needed
+                            the stop-the-world fallback                    */
+};
+
+typedef void *phos_stream_t;             /* a cudaStream_t */
+
+/* One buffer of the process (Sec. 2.1: a contiguous virtual range per
+ * allocation; Sec. 4.1: the OS learns them by intercepting allocation). */
+typedef struct {
+    uint64_t base;                        /* first byte                    */
+    uint64_t size;                        /* bytes, > 0                    */
+} phos_buf_t;
+
+/* Speculated permission per buffer (Sec. 4.1 write set, Sec. 6 read set).
+ * A mutable pointer argument both reads and writes its buffer.           */
+enum { PHOS_PERM_NONE = 0, PHOS_PERM_R = 1, PHOS_PERM_W = 2, PHOS_PERM_RW = 3 };
+
+/* Kind of a launch argument (Sec. 4.1: the kernel signature tells pointer
+ * from scalar and const from mutable; an opaque struct is scanned in
+ * 8-byte chunks, each a possible mutable pointer).                      */
+enum { PHOS_ARG_SCALAR = 0, PHOS_ARG_CONST_PTR = 1, PHOS_ARG_MUT_PTR = 2,
+       PHOS_ARG_STRUCT = 3 };
+
+/* Trace record: bit 63 = store, bits 57..62 reserved (must be 0),
+ * bits 0..56 = the accessed address.                                     */
+#define PHOS_REC_STORE (1ull << 63)
+#define PHOS_REC_ADDR_MASK ((1ull << 57) - 1ull)
+
+/* Copy descriptor: one (buffer, offset, len) region (Sec. 4.2 CoW copy,
+ * Sec. 4.3 recopy, Sec. 5 4 MB chunks, Sec. 6 restore).  A live endpoint is
+ * (table index buf, offset inside that buffer); a staging or image
+ * endpoint is a byte offset into the staging or image area of the call.  */
+typedef struct {
+    uint64_t src_off;
+    uint64_t dst_off;
+    uint64_t len;
+    uint32_t buf;
+    uint32_t flags;                       /* PHOS_COPY_* direction | marks  */
+} phos_copy_t;
+enum {
+    PHOS_COPY_LIVE_TO_STAGING = 1,        /* CoW: buffer -> device staging  */
+    PHOS_COPY_LIVE_TO_IMAGE = 2,          /* checkpoint / recopy            */
+    PHOS_COPY_STAGING_TO_IMAGE = 3,       /* drain a CoW shadow             */
+    PHOS_COPY_IMAGE_TO_LIVE = 4,          /* restore                        */
+    PHOS_COPY_DIR_MASK = 0xff,
+    PHOS_COPY_MARK_PRESENT = 0x100        /* set bit buf of the present
+                                             bitmap once these bytes landed */
+};
+
+const char *phos_last_error(void);
+const char *phos_status_name(phos_status s);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (diagnostics: lets a caller count launches inside a timed region). */
+uint64_t phos_launch_count(void);
+
+/* ---------------------------------------------------------------- table */
+
+typedef struct phos_table phos_table_t;
+
+/* Copy n buffers (host array, sorted by base, disjoint, size > 0, inside
+ * the 57-bit address space) into a device-resident table.  Synchronous.
+ * EINVAL if the rules are broken; n may be 0 (every access then fails
+ * validation as unmapped).  The table keeps a host copy for speculation. */
+phos_status phos_table_create(const phos_buf_t *bufs, uint32_t n, phos_table_t **out);
+phos_status phos_table_destroy(phos_table_t *t);
+uint32_t phos_table_size(const phos_table_t *t);
+
+/* ----------------------------------------------------------- speculate */
+
+/* Argument-based speculation (Sec. 4.1, Sec. 6), host side.
+ * args[j] points at the bytes of argument j (arg_size[j] bytes, little
+ * endian), kind[j] is PHOS_ARG_*.  Pointer arguments use their first 8
+ * bytes (zero-extended if shorter); a struct is scanned at offsets 0, 8,
+ * ... and a trailing partial chunk is ignored.  Every value v with
+ * base <= v < base + size marks that buffer R (const) or RW (mutable,
+ * struct).  perm_out (host, n bytes) is OR-accumulated: zero it first. */
+phos_status phos_speculate(const phos_table_t *t, const void *const *args,
+                           const uint32_t *arg_size, const uint8_t *kind,
+                           uint32_t nargs, uint8_t *perm_out);
+
+/* Type-1 APIs (Sec. 4.1, memory moves): a call that reads or writes
+ * [addr, addr + len) marks every buffer the range overlaps with perm. */
+phos_status phos_speculate_region(const phos_table_t *t, uint64_t addr, uint64_t len,
+                                  uint8_t perm, uint8_t *perm_out);
+
+/* ------------------------------------------------------------ validate */
+
+/* Access validation (Sec. 4.1 "Runtime validation"; reads too, Sec. 6).
+ * For each record r of d_trace (n_rec records, 16-byte aligned device
+ * array): find the buffer i with base_i <= a and a + access_bytes <=
+ * base_i + size_i.  Outcomes:
+ *   no such buffer (gap, straddle, or reserved bits set) -> violation,
+ *       counted in d_count[2] ("unmapped"; reserved bits also make the
+ *       status word PHOS_EINVAL)
+ *   load and !(d_perm[i] & R), or store and !(d_perm[i] & W)
+ *       -> violation; bit i set in d_victim, and in d_victim_st if a store
+ * d_bitmap (u32[ceil(n_rec/32)]): bit r&31 of word r>>5 set per violation,
+ *   padding bits 0.  d_count (u64[3]): violations, store violations,
+ *   unmapped violations.  d_victim, d_victim_st (u32[ceil(n/32)]) and d_idx
+ *   (the first idx_cap violating r, ascending) may be NULL.
+ * All outputs are overwritten.  d_perm: device u8[n].  access_bytes >= 1.
+ * Asynchronous on stream; uses the table handle's scratch. */
+phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
+                          const uint64_t *d_trace, uint64_t n_rec, uint32_t access_bytes,
+                          uint32_t *d_bitmap, uint64_t *d_count, uint32_t *d_victim,
+                          uint32_t *d_victim_st, uint64_t *d_idx, uint64_t idx_cap,
+                          uint32_t *d_status, phos_stream_t stream);
+
+/* --------------------------------------------------------- copy engine */
+
+/* Gather-copy n descriptors (d_list: device array) between live buffers,
+ * the staging area and the image.  Bounds: live off + len <= size[buf];
+ * staging / image off + len <= their byte sizes.  A descriptor that breaks
+ * a rule, or whose direction the entry point does not allow, moves nothing
+ * and sets PHOS_EINVAL in d_status; the others still run.  Source and
+ * destination must not overlap.  Asynchronous on stream.
+ *
+ * phos_cow_copy            live -> staging only (Sec. 4.2 copy-on-write)
+ * phos_recopy              live -> image only (Sec. 4.3 recopy; also the
+ *                          bulk checkpoint copy of Sec. 4.2/5)
+ * phos_restore_on_demand   image -> live only (Sec. 6); descriptors with
+ *                          PHOS_COPY_MARK_PRESENT set bit buf of d_present
+ *                          (u32[ceil(n/32)], device) after their bytes land
+ * phos_copy                any direction, mixed in one launch (the
+ *                          background copier: shadow or live -> image) */
+phos_status phos_cow_copy(const phos_table_t *t, const phos_copy_t *d_list, uint32_t n,
+                          void *d_staging, uint64_t staging_bytes, uint32_t *d_status,
+                          phos_stream_t stream);
+phos_status phos_recopy(const phos_table_t *t, const phos_copy_t *d_list, uint32_t n,
+                        void *image, uint64_t image_bytes, uint32_t *d_status,
+                        phos_stream_t stream);
+phos_status phos_restore_on_demand(const phos_table_t *t, const phos_copy_t *d_list, uint32_t n,
+                                   const void *image, uint64_t image_bytes,
+                                   uint32_t *d_present, uint32_t *d_status,
+                                   phos_stream_t stream);
+phos_status phos_copy(const phos_table_t *t, const phos_copy_t *d_list, uint32_t n,
+                      void *d_staging, uint64_t staging_bytes, void *image,
+                      uint64_t image_bytes, uint32_t *d_present, uint32_t *d_status,
+                      phos_stream_t stream);
+
+/* Launch shape of the copy engine: tile_bytes per CTA work item (multiple
+ * of 4096, 4 KiB..16 MiB) and CTAs per SM (1..8).  Process-wide; the
+ * autotuner sets it.  0 leaves a field unchanged. */
+phos_status phos_copy_config(uint64_t tile_bytes, uint32_t ctas_per_sm);
+
+/* Image layout used by the protocols: buffer i at img_off[i] = sum of
+ * align256(size) of the buffers before it; returns the total bytes. */
+uint64_t phos_image_bytes(const phos_table_t *t);
+phos_status phos_image_offsets(const phos_table_t *t, uint64_t *img_off_out);
+
+/* ------------------------------------------------- protocol control plane
+ *
+ * Lockstep drivers of the three concurrent protocols.  The caller plays
+ * the application: between phos_*_before_kernel and phos_*_after_kernel it
+ * launches its kernel on the same stream.  A "round" is: advance (the
+ * background copier moves up to quota bytes), before_kernel (the protocol
+ * acts on the kernel's speculated buffers), the caller's kernel,
+ * after_kernel (validation of the kernel's access trace and the
+ * mis-speculation rules).  Copier order: ascending table index, pieces of
+ * at most `chunk` bytes that never cross a buffer and are cut at the
+ * remaining quota; each piece charges align256(len) against the quota.
+ * Image layout: phos_image_offsets.  Only after_kernel, finish and the
+ * fallbacks synchronise the stream. */
+
+typedef struct phos_ckpt phos_ckpt_t;
+typedef struct phos_restore phos_restore_t;
+
+enum { PHOS_CKPT_COW = 1, PHOS_CKPT_RECOPY = 2 };
+
+typedef struct {
+    uint32_t mode;           /* PHOS_CKPT_COW (Sec. 4.2) or PHOS_CKPT_RECOPY
+                                (Sec. 4.3)                                   */
+    uint32_t access_bytes;   /* width of every traced access (>= 1)          */
+    uint64_t chunk;          /* copier piece size, multiple of 256 (Sec. 5
+                                uses 4 MiB)                                 */
+    void *d_staging;         /* CoW staging area (device); may be NULL       */
+    uint64_t staging_bytes;  /* CoW budget (Sec. 4.2 reserves up to 2 GB)    */
+    void *image;             /* destination, >= phos_image_bytes(t) bytes    */
+    uint64_t image_bytes;
+} phos_ckpt_desc_t;
+
+typedef struct {
+    uint64_t kernels;        /* rounds begun (before_kernel calls)           */
+    uint64_t copier_bytes;   /* bytes the background copier moved            */
+    uint64_t cow_bytes;      /* CoW copies into staging                      */
+    uint64_t direct_bytes;   /* CoW with no room: straight to the image      */
+    uint64_t recopy_bytes;   /* recopy at t2                                 */
+    uint64_t validated;      /* trace records validated                      */
+    uint64_t violations;     /* of which violations                          */
+    int64_t misspec_round;   /* round whose validation forced the
+                                stop-the-world fallback, or -1               */
+    uint32_t done;           /* 1 once the image is complete                 */
+    uint32_t dirty;          /* recopy: size of the dirty set                */
+} phos_ckpt_stats_t;
+
+/* Start a checkpoint at t1 (the caller has quiesced: Sec. 4.2 phase 1).
+ * Every buffer is pending.  Allocates the session's device and pinned
+ * scratch. */
+phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_desc_t *d,
+                            phos_stream_t stream, phos_ckpt_t **out);
+/* Background copier: up to quota bytes (shadow if one exists, else live ->
+ * image).  *done = 1 once every buffer is in the image. */
+phos_status phos_ckpt_advance(phos_ckpt_t *c, uint64_t quota, int *done);
+/* perm: host u8[n] speculated for the next kernel.  CoW: every speculated
+ * write buffer that is neither done nor shadowed is copied whole to
+ * staging (first fit, align256(size)) or, without room, its remaining
+ * bytes go straight to the image (Sec. 4.2).  Recopy: speculated write
+ * buffers that are in flight or done join the dirty set (Sec. 4.3). */
+phos_status phos_ckpt_before_kernel(phos_ckpt_t *c, const uint8_t *perm);
+/* Validate the kernel's trace (device, 16-byte aligned) against perm;
+ * synchronises.  CoW: a store victim that was neither done nor shadowed
+ * before the kernel discards the checkpoint and copies every buffer
+ * stop-the-world now; *misspec = 1 and the session is complete.  Recopy:
+ * store victims that were in flight or done join the dirty set. */
+phos_status phos_ckpt_after_kernel(phos_ckpt_t *c, const uint64_t *d_trace, uint64_t n_rec,
+                                   int *misspec);
+/* Drain the rest; recopy: quiesce point t2, recopy the dirty set whole.
+ * Synchronises. */
+phos_status phos_ckpt_finish(phos_ckpt_t *c);
+phos_status phos_ckpt_stats(const phos_ckpt_t *c, phos_ckpt_stats_t *out);
+/* Event logs, 5 u64 per event (n_out = number of events available):
+ *   0 CoW:     round, buffer, 1 = staging / 2 = direct, offset, len
+ *   1 copier:  round, buffer, offset in buffer, len, 1 if from a shadow
+ *   2 dirty:   buffer, 0, 0, 0, 0 (ascending)                            */
+phos_status phos_ckpt_log(const phos_ckpt_t *c, uint32_t kind, uint64_t *out, uint64_t cap,
+                          uint64_t *n_out);
+phos_status phos_ckpt_end(phos_ckpt_t *c);
+
+typedef struct {
+    uint32_t access_bytes;
+    uint32_t reserved;
+    uint64_t chunk;          /* multiple of 256                              */
+    const void *image;       /* checkpoint image (pinned host or device)     */
+    uint64_t image_bytes;
+    uint32_t *d_present;     /* optional device u32[ceil(n/32)] kept in step
+                                with the restored set (zeroed by begin)      */
+} phos_restore_desc_t;
+
+typedef struct {
+    uint64_t kernels;
+    uint64_t copier_bytes;   /* background bulk restore                      */
+    uint64_t ondemand_bytes; /* copied before a kernel that needed them      */
+    uint64_t validated;
+    uint64_t violations;
+    int64_t misspec_round;
+    uint32_t done;           /* every buffer present                         */
+    uint32_t reserved;
+} phos_restore_stats_t;
+
+/* Concurrent restore (Sec. 6): nothing is present at begin. */
+phos_status phos_restore_begin(const phos_table_t *t, const phos_restore_desc_t *d,
+                               phos_stream_t stream, phos_restore_t **out);
+/* Background bulk restore of up to quota bytes, skipping present buffers
+ * and never writing one.  *done = 1 once every buffer is present. */
+phos_status phos_restore_advance(phos_restore_t *r, uint64_t quota, int *done);
+/* Copy the not-yet-restored bytes of every buffer with perm != 0 before
+ * the kernel runs (the kernel waits for them). */
+phos_status phos_restore_before_kernel(phos_restore_t *r, const uint8_t *perm);
+/* Validate; an access (load or store) to a buffer that was not present
+ * before the kernel restores every buffer stop-the-world from the image
+ * and sets *misspec = 1: the caller replays its kernels from the first
+ * (Sec. 6 "roll back ... and perform a stop-the-world restore").
+ * Synchronises. */
+phos_status phos_restore_after_kernel(phos_restore_t *r, const uint64_t *d_trace,
+                                      uint64_t n_rec, int *misspec);
+phos_status phos_restore_finish(phos_restore_t *r);
+phos_status phos_restore_stats(const phos_restore_t *r, phos_restore_stats_t *out);
+/* kind 0 on-demand: round, buffer, offset, len, 0;
+ * kind 1 copier: round, buffer, offset, len, 0 */
+phos_status phos_restore_log(const phos_restore_t *r, uint32_t kind, uint64_t *out,
+                             uint64_t cap, uint64_t *n_out);
+phos_status phos_restore_end(phos_restore_t *r);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHOS_H */

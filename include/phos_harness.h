@@ -1,0 +1,54 @@
+/*
+ * phos_harness.h -- test and benchmark harness kernels of the PhOS data
+ * plane library.  Not part of the method: these stand in for the
+ * application whose memory is checkpointed (the paper's evaluation runs
+ * real training and inference jobs, Table 4), and give an exact,
+ * order-independent fingerprint of memory so that images can be compared
+ * without copying them back.
+ *
+ * Definitions (SplitMix64 of Steele, Lea & Flood, OOPSLA 2014:
+ * mix64 = its output function, sm(x) = mix64(x + 0x9E3779B97F4A7C15)):
+ *   digest   D(bytes) = sum over 8-byte little-endian words j of
+ *            mix64(word_j + j * 0x9E3779B97F4A7C15) mod 2^64, the last word
+ *            zero-padded.
+ *   mutator  kernel k reading buffers r (ascending) and writing buffers w:
+ *            s_k = sm(seed ^ sm(k)), then s_k = sm(s_k ^ D(r)) per read;
+ *            word j of each written buffer w = sm(sm(s_k ^ sm(w)) ^ j),
+ *            little-endian, tail truncated; then each stray store (record
+ *            index r, address a) writes the low 32 bits of
+ *            sm(sm(seed ^ k) ^ r) at a, in list order.
+ * All calls are asynchronous on the stream and return PHOS_* codes.
+ */
+#ifndef PHOS_HARNESS_H
+#define PHOS_HARNESS_H
+
+#include "phos.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Digest n regions: ptrs[j] (device-accessible address; pinned host memory
+ * is translated), lens[j] bytes (host arrays).  d_out: device u64[n],
+ * overwritten. */
+phos_status phos_harness_digest(const uint64_t *ptrs, const uint64_t *lens, uint32_t n,
+                                uint64_t *d_out, phos_stream_t stream);
+
+/* Run mutator kernel k over the table's buffers: reads (ascending table
+ * indices, host array, the written buffers included) and writes (host
+ * array), then ns stray stores d_strays[2*q] = record index,
+ * d_strays[2*q + 1] = address (device array).  Each stray must lie inside
+ * a table buffer (4 bytes). */
+phos_status phos_harness_mutate(const phos_table_t *t, uint64_t seed, uint64_t k,
+                                const uint32_t *reads, uint32_t nr, const uint32_t *writes,
+                                uint32_t nw, const uint64_t *d_strays, uint32_t ns,
+                                phos_stream_t stream);
+
+/* Fill [ptr, ptr + len) (device address) with bytes of sm(key ^ j) words:
+ * used to give live memory and arenas a reproducible initial content. */
+phos_status phos_harness_fill(uint64_t ptr, uint64_t len, uint64_t key, phos_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHOS_HARNESS_H */

@@ -1,0 +1,692 @@
+// Host control plane: lockstep drivers of soft copy-on-write (PhoenixOS
+// Sec. 4.2), soft recopy (Sec. 4.3) and soft on-demand concurrent restore
+// (Sec. 6).  The state machines run on the host (buffer states, the CoW
+// shadow map, the dirty set, the present set); every byte moves through
+// the copy engine and every trace through the validator, on the caller's
+// stream.  Copy lists are staged in a pinned host arena and uploaded with
+// one asynchronous copy per batch; the arena is recycled at the stream
+// synchronisations that after_kernel performs anyway to read the victims.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace phos {
+
+enum : uint8_t { kPending = 0, kInflight = 1, kDone = 2 };
+
+// First fit over free extents sorted by offset, coalesced on release.
+struct FirstFit {
+    std::vector<std::pair<uint64_t, uint64_t>> free;  // (off, len)
+    explicit FirstFit(uint64_t total) {
+        if (total) free.push_back({0, total});
+    }
+    bool alloc(uint64_t need, uint64_t *off) {
+        for (size_t j = 0; j < free.size(); ++j) {
+            if (free[j].second >= need) {
+                *off = free[j].first;
+                if (free[j].second == need)
+                    free.erase(free.begin() + j);
+                else
+                    free[j] = {free[j].first + need, free[j].second - need};
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t len) {
+        auto it = std::lower_bound(free.begin(), free.end(), std::make_pair(off, (uint64_t)0));
+        it = free.insert(it, {off, len});
+        size_t j = it - free.begin();
+        if (j + 1 < free.size() && free[j].first + free[j].second == free[j + 1].first) {
+            free[j].second += free[j + 1].second;
+            free.erase(free.begin() + j + 1);
+        }
+        if (j > 0 && free[j - 1].first + free[j - 1].second == free[j].first) {
+            free[j - 1].second += free[j].second;
+            free.erase(free.begin() + j);
+        }
+    }
+};
+
+// Device and pinned resources shared by the sessions.
+struct Session {
+    const phos_table *t = nullptr;
+    cudaStream_t s = nullptr;
+    uint32_t n = 0, w = 4;
+    uint64_t chunk = 4ull << 20;
+    // pinned host arena for copy lists (recycled at synchronisations)
+    phos_copy_t *h_list = nullptr;
+    size_t h_cap = 0, h_used = 0;
+    phos_copy_t *d_list = nullptr;
+    size_t d_cap = 0;
+    // validator I/O
+    uint8_t *h_perm = nullptr, *d_perm = nullptr;
+    uint32_t *d_bitmap = nullptr;
+    uint64_t bitmap_words = 0;
+    uint64_t *h_count = nullptr;      // pinned mapped: count[3]
+    uint32_t *h_victim = nullptr;     // pinned mapped: victim | victim_st
+    uint32_t *h_status = nullptr;     // pinned mapped
+    uint64_t *d_count = nullptr;
+    uint32_t *d_victim = nullptr, *d_status = nullptr;
+    // copier
+    std::vector<uint8_t> state;
+    std::vector<uint64_t> copied;
+    uint32_t cursor = 0;
+    uint64_t round = 0;
+    std::vector<uint64_t> copier_log;
+    uint64_t validated = 0, violations = 0;
+
+    phos_status init(const phos_table *tt, cudaStream_t ss, uint32_t ww, uint64_t ch) {
+        t = tt;
+        s = ss;
+        n = tt->n;
+        w = ww;
+        chunk = ch;
+        state.assign(n, kPending);
+        copied.assign(n, 0);
+        const uint32_t nvw = (n + 31) / 32;
+        PHOS_CUDA(cudaHostAlloc(&h_perm, std::max(n, 1u), cudaHostAllocDefault));
+        PHOS_CUDA(cudaMalloc(&d_perm, std::max(n, 1u)));
+        PHOS_CUDA(cudaHostAlloc(&h_count, 64, cudaHostAllocMapped));
+        PHOS_CUDA(cudaHostAlloc(&h_victim, 8ull * std::max(nvw, 1u), cudaHostAllocMapped));
+        PHOS_CUDA(cudaHostAlloc(&h_status, 64, cudaHostAllocMapped));
+        PHOS_CUDA(cudaHostGetDevicePointer((void **)&d_count, h_count, 0));
+        PHOS_CUDA(cudaHostGetDevicePointer((void **)&d_victim, h_victim, 0));
+        PHOS_CUDA(cudaHostGetDevicePointer((void **)&d_status, h_status, 0));
+        *h_status = 0;
+        return reserve_list(1024);
+    }
+
+    ~Session() {
+        if (s) cudaStreamSynchronize(s);
+        if (h_list) cudaFreeHost(h_list);
+        if (d_list) cudaFree(d_list);
+        if (h_perm) cudaFreeHost(h_perm);
+        if (d_perm) cudaFree(d_perm);
+        if (d_bitmap) cudaFree(d_bitmap);
+        if (h_count) cudaFreeHost(h_count);
+        if (h_victim) cudaFreeHost(h_victim);
+        if (h_status) cudaFreeHost(h_status);
+    }
+
+    phos_status reserve_list(size_t need) {
+        if (need <= h_cap) return PHOS_OK;
+        size_t cap = std::max(need, 2 * h_cap);
+        if (h_list) {
+            PHOS_CUDA(cudaStreamSynchronize(s));
+            cudaFreeHost(h_list);
+            cudaFree(d_list);
+            h_used = 0;
+        }
+        PHOS_CUDA(cudaHostAlloc(&h_list, cap * sizeof(phos_copy_t), cudaHostAllocDefault));
+        PHOS_CUDA(cudaMalloc(&d_list, cap * sizeof(phos_copy_t)));
+        h_cap = d_cap = cap;
+        return PHOS_OK;
+    }
+
+    // Launch one batch through the copy engine.
+    phos_status submit(const std::vector<phos_copy_t> &v, void *staging, uint64_t staging_bytes,
+                       const void *image, uint64_t image_bytes, uint32_t *present) {
+        if (v.empty()) return PHOS_OK;
+        if (h_used + v.size() > h_cap) {
+            PHOS_CUDA(cudaStreamSynchronize(s));
+            h_used = 0;
+            phos_status r = reserve_list(v.size());
+            if (r) return r;
+        }
+        phos_copy_t *hp = h_list + h_used;
+        phos_copy_t *dp = d_list + h_used;
+        memcpy(hp, v.data(), v.size() * sizeof(phos_copy_t));
+        PHOS_CUDA(cudaMemcpyAsync(dp, hp, v.size() * sizeof(phos_copy_t), cudaMemcpyHostToDevice,
+                                  s));
+        h_used += v.size();
+        return phos_copy(t, dp, (uint32_t)v.size(), staging, staging_bytes,
+                         const_cast<void *>(image), image_bytes, present, d_status, s);
+    }
+
+    phos_status sync() {
+        PHOS_CUDA(cudaStreamSynchronize(s));
+        h_used = 0;
+        if (*h_status) return fail((phos_status)*h_status, "device reported %s",
+                                   phos_status_name((phos_status)*h_status));
+        return PHOS_OK;
+    }
+
+    // perm for the next kernel -> device
+    phos_status stage_perm(const uint8_t *perm) {
+        if (!perm && n) return fail(PHOS_EINVAL, "perm is NULL");
+        if (n) {
+            memcpy(h_perm, perm, n);
+            PHOS_CUDA(cudaMemcpyAsync(d_perm, h_perm, n, cudaMemcpyHostToDevice, s));
+        }
+        return PHOS_OK;
+    }
+
+    // Validate and wait: fills h_count and h_victim (victim | victim_st).
+    phos_status validate_sync(const uint64_t *d_trace, uint64_t n_rec) {
+        const uint64_t words = std::max<uint64_t>((n_rec + 31) / 32, 1);
+        if (words > bitmap_words) {
+            PHOS_CUDA(cudaStreamSynchronize(s));
+            if (d_bitmap) cudaFree(d_bitmap);
+            PHOS_CUDA(cudaMalloc(&d_bitmap, words * 4));
+            bitmap_words = words;
+        }
+        const uint32_t nvw = (n + 31) / 32;
+        phos_status r = phos_validate(t, d_perm, d_trace, n_rec, w, d_bitmap, d_count, d_victim,
+                                      d_victim + std::max(nvw, 1u), nullptr, 0, d_status, s);
+        if (r) return r;
+        r = sync();
+        if (r) return r;
+        validated += n_rec;
+        violations += h_count[0];
+        return PHOS_OK;
+    }
+
+    bool victim_bit(bool store_only, uint32_t i) const {
+        const uint32_t nvw = std::max((n + 31) / 32, 1u);
+        const uint32_t *v = h_victim + (store_only ? nvw : 0);
+        return (v[i >> 5] >> (i & 31)) & 1u;
+    }
+
+    bool done() {
+        while (cursor < n && state[cursor] == kDone) ++cursor;
+        return cursor >= n;
+    }
+
+    // One copier advance; piece(i, off, len) appends a descriptor and
+    // returns whether it came from a shadow; skip(i) marks i done untouched.
+    template <typename Piece, typename Skip>
+    uint64_t advance(uint64_t quota, Piece piece, Skip skip) {
+        uint64_t left = quota, moved = 0;
+        while (left > 0 && !done()) {
+            const uint32_t i = cursor;
+            if (skip(i)) {
+                state[i] = kDone;
+                continue;
+            }
+            const uint64_t rem = t->size[i] - copied[i];
+            const uint64_t take = std::min(std::min(chunk, rem), left);
+            if (take == 0) break;
+            const bool sh = piece(i, copied[i], take);
+            copier_log.insert(copier_log.end(), {round, i, copied[i], take, sh ? 1ull : 0ull});
+            copied[i] += take;
+            moved += take;
+            const uint64_t charge = align_up(take, 256);
+            left = charge >= left ? 0 : left - charge;
+            state[i] = copied[i] == t->size[i] ? kDone : kInflight;
+        }
+        return moved;
+    }
+};
+
+phos_status copy_log(const std::vector<uint64_t> &log, uint64_t *out, uint64_t cap,
+                     uint64_t *n_out) {
+    const uint64_t ev = log.size() / 5;
+    if (n_out) *n_out = ev;
+    if (out) memcpy(out, log.data(), 8 * 5 * std::min(ev, cap));
+    return PHOS_OK;
+}
+
+}  // namespace phos
+
+using namespace phos;
+
+struct phos_ckpt {
+    Session ss;
+    uint32_t mode = PHOS_CKPT_COW;
+    void *staging = nullptr;
+    uint64_t staging_bytes = 0;
+    void *image = nullptr;
+    uint64_t image_bytes = 0;
+    FirstFit alloc{0};
+    std::vector<int64_t> shadow;   // staging offset or -1
+    std::vector<uint8_t> safe;     // CoW: done or shadowed when the kernel ran
+    std::vector<uint8_t> touched;  // recopy: in flight or done when the kernel ran
+    std::vector<uint8_t> dirty;
+    std::vector<uint64_t> cow_log;
+    uint64_t cow_bytes = 0, direct_bytes = 0, copier_bytes = 0, recopy_bytes = 0;
+    int64_t misspec = -1;
+    bool complete = false, finished = false, in_kernel = false;
+};
+
+extern "C" phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_desc_t *d,
+                                       phos_stream_t stream, phos_ckpt_t **out) {
+    if (!t || !d || !out) return fail(PHOS_EINVAL, "ckpt_begin: NULL argument");
+    *out = nullptr;
+    if (d->mode != PHOS_CKPT_COW && d->mode != PHOS_CKPT_RECOPY)
+        return fail(PHOS_EINVAL, "ckpt_begin: mode %u", d->mode);
+    if (d->access_bytes == 0 || d->chunk == 0 || d->chunk % 256)
+        return fail(PHOS_EINVAL, "ckpt_begin: access_bytes >= 1, chunk a multiple of 256");
+    if (!d->image || d->image_bytes < t->image_bytes)
+        return fail(PHOS_EINVAL, "ckpt_begin: image smaller than %llu bytes",
+                    (unsigned long long)t->image_bytes);
+    phos_ckpt *c = new phos_ckpt();
+    phos_status r = c->ss.init(t, static_cast<cudaStream_t>(stream), d->access_bytes, d->chunk);
+    if (r) {
+        delete c;
+        return r;
+    }
+    c->mode = d->mode;
+    c->staging = d->mode == PHOS_CKPT_COW ? d->d_staging : nullptr;
+    c->staging_bytes = c->staging ? d->staging_bytes : 0;
+    c->image = d->image;
+    c->image_bytes = d->image_bytes;
+    c->alloc = FirstFit(c->staging_bytes);
+    c->shadow.assign(t->n, -1);
+    c->safe.assign(t->n, 0);
+    c->touched.assign(t->n, 0);
+    c->dirty.assign(t->n, 0);
+    c->complete = t->n == 0;
+    *out = c;
+    return PHOS_OK;
+}
+
+static phos_status ckpt_advance(phos_ckpt *c, uint64_t quota) {
+    Session &S = c->ss;
+    const phos_table *t = S.t;
+    std::vector<phos_copy_t> v;
+    uint64_t moved = S.advance(
+        quota,
+        [&](uint32_t i, uint64_t off, uint64_t len) {
+            const int64_t sh = c->shadow[i];
+            phos_copy_t d;
+            d.len = len;
+            d.buf = i;
+            d.dst_off = t->img_off[i] + off;
+            if (sh >= 0) {
+                d.src_off = (uint64_t)sh + off;
+                d.flags = PHOS_COPY_STAGING_TO_IMAGE;
+            } else {
+                d.src_off = off;
+                d.flags = PHOS_COPY_LIVE_TO_IMAGE;
+            }
+            v.push_back(d);
+            if (off + len == t->size[i] && sh >= 0) {
+                // the drain is stream-ordered before any later reuse
+                c->alloc.release((uint64_t)sh, align_up(t->size[i], 256));
+                c->shadow[i] = -1;
+            }
+            return sh >= 0;
+        },
+        [](uint32_t) { return false; });
+    c->copier_bytes += moved;
+    return S.submit(v, c->staging, c->staging_bytes, c->image, c->image_bytes, nullptr);
+}
+
+extern "C" phos_status phos_ckpt_advance(phos_ckpt_t *c, uint64_t quota, int *done) {
+    if (!c) return fail(PHOS_EINVAL, "ckpt_advance: NULL session");
+    if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_advance: inside a kernel round");
+    phos_status r = PHOS_OK;
+    if (!c->complete) {
+        r = ckpt_advance(c, quota);
+        if (c->ss.done()) c->complete = true;
+    }
+    if (done) *done = c->complete ? 1 : 0;
+    return r;
+}
+
+extern "C" phos_status phos_ckpt_before_kernel(phos_ckpt_t *c, const uint8_t *perm) {
+    if (!c) return fail(PHOS_EINVAL, "ckpt_before_kernel: NULL session");
+    if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_before_kernel: after_kernel missing");
+    if (c->complete) return fail(PHOS_EINVAL, "ckpt_before_kernel: checkpoint already complete");
+    Session &S = c->ss;
+    const phos_table *t = S.t;
+    phos_status r = S.stage_perm(perm);
+    if (r) return r;
+    const uint32_t n = S.n;
+    if (c->mode == PHOS_CKPT_COW) {
+        std::vector<phos_copy_t> v;
+        for (uint32_t i = 0; i < n; ++i) {
+            if (!(perm[i] & PHOS_PERM_W)) continue;
+            if (S.state[i] == kDone || c->shadow[i] >= 0) continue;
+            const uint64_t sz = t->size[i];
+            uint64_t off;
+            phos_copy_t d;
+            d.buf = i;
+            if (c->alloc.alloc(align_up(sz, 256), &off)) {
+                c->shadow[i] = (int64_t)off;
+                d.src_off = 0;
+                d.dst_off = off;
+                d.len = sz;
+                d.flags = PHOS_COPY_LIVE_TO_STAGING;
+                c->cow_log.insert(c->cow_log.end(), {S.round, i, 1ull, off, sz});
+                c->cow_bytes += sz;
+            } else {
+                const uint64_t cp = S.copied[i];
+                d.src_off = cp;
+                d.dst_off = t->img_off[i] + cp;
+                d.len = sz - cp;
+                d.flags = PHOS_COPY_LIVE_TO_IMAGE;
+                c->cow_log.insert(c->cow_log.end(), {S.round, i, 2ull, cp, sz - cp});
+                c->direct_bytes += sz - cp;
+                S.copied[i] = sz;
+                S.state[i] = kDone;
+            }
+            v.push_back(d);
+        }
+        for (uint32_t i = 0; i < n; ++i) c->safe[i] = S.state[i] == kDone || c->shadow[i] >= 0;
+        r = S.submit(v, c->staging, c->staging_bytes, c->image, c->image_bytes, nullptr);
+        if (r) return r;
+    } else {
+        for (uint32_t i = 0; i < n; ++i) {
+            c->touched[i] = S.state[i] != kPending;
+            if ((perm[i] & PHOS_PERM_W) && c->touched[i]) c->dirty[i] = 1;
+        }
+    }
+    c->in_kernel = true;
+    return PHOS_OK;
+}
+
+static phos_status stw_checkpoint(phos_ckpt *c) {
+    Session &S = c->ss;
+    std::vector<phos_copy_t> v;
+    for (uint32_t i = 0; i < S.n; ++i) {
+        phos_copy_t d;
+        d.src_off = 0;
+        d.dst_off = S.t->img_off[i];
+        d.len = S.t->size[i];
+        d.buf = i;
+        d.flags = PHOS_COPY_LIVE_TO_IMAGE;
+        v.push_back(d);
+        S.state[i] = kDone;
+        S.copied[i] = S.t->size[i];
+    }
+    phos_status r = S.submit(v, nullptr, 0, c->image, c->image_bytes, nullptr);
+    if (r) return r;
+    return S.sync();
+}
+
+extern "C" phos_status phos_ckpt_after_kernel(phos_ckpt_t *c, const uint64_t *d_trace,
+                                              uint64_t n_rec, int *misspec) {
+    if (!c) return fail(PHOS_EINVAL, "ckpt_after_kernel: NULL session");
+    if (!c->in_kernel) return fail(PHOS_EINVAL, "ckpt_after_kernel: before_kernel missing");
+    Session &S = c->ss;
+    c->in_kernel = false;
+    const uint64_t k = S.round++;
+    if (misspec) *misspec = 0;
+    phos_status r = S.validate_sync(d_trace, n_rec);
+    if (r) return r;
+    if (S.h_count[1] == 0) return PHOS_OK;  // no store violated the speculation
+    if (c->mode == PHOS_CKPT_COW) {
+        for (uint32_t i = 0; i < S.n; ++i) {
+            if (S.victim_bit(true, i) && !c->safe[i]) {
+                c->misspec = (int64_t)k;
+                r = stw_checkpoint(c);
+                if (r) return r;
+                c->complete = true;
+                for (uint32_t j = 0; j < S.n; ++j)
+                    if (c->shadow[j] >= 0) c->shadow[j] = -1;
+                if (misspec) *misspec = 1;
+                return PHOS_OK;
+            }
+        }
+    } else {
+        for (uint32_t i = 0; i < S.n; ++i)
+            if (S.victim_bit(true, i) && c->touched[i]) c->dirty[i] = 1;
+    }
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_ckpt_finish(phos_ckpt_t *c) {
+    if (!c) return fail(PHOS_EINVAL, "ckpt_finish: NULL session");
+    if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_finish: inside a kernel round");
+    Session &S = c->ss;
+    phos_status r;
+    if (!c->complete && c->misspec < 0) {
+        r = ckpt_advance(c, ~0ull >> 2);
+        if (r) return r;
+        c->complete = S.done();
+    }
+    if (c->mode == PHOS_CKPT_RECOPY && !c->finished) {
+        // t2: quiesce (the caller has stopped issuing kernels), recopy the
+        // dirty buffers whole from live memory
+        std::vector<phos_copy_t> v;
+        for (uint32_t i = 0; i < S.n; ++i) {
+            if (!c->dirty[i]) continue;
+            phos_copy_t d;
+            d.src_off = 0;
+            d.dst_off = S.t->img_off[i];
+            d.len = S.t->size[i];
+            d.buf = i;
+            d.flags = PHOS_COPY_LIVE_TO_IMAGE;
+            v.push_back(d);
+            c->recopy_bytes += S.t->size[i];
+        }
+        r = S.submit(v, nullptr, 0, c->image, c->image_bytes, nullptr);
+        if (r) return r;
+    }
+    c->finished = true;
+    return S.sync();
+}
+
+extern "C" phos_status phos_ckpt_stats(const phos_ckpt_t *c, phos_ckpt_stats_t *o) {
+    if (!c || !o) return fail(PHOS_EINVAL, "ckpt_stats: NULL argument");
+    memset(o, 0, sizeof *o);
+    o->kernels = c->ss.round;
+    o->copier_bytes = c->copier_bytes;
+    o->cow_bytes = c->cow_bytes;
+    o->direct_bytes = c->direct_bytes;
+    o->recopy_bytes = c->recopy_bytes;
+    o->validated = c->ss.validated;
+    o->violations = c->ss.violations;
+    o->misspec_round = c->misspec;
+    o->done = c->complete ? 1 : 0;
+    uint32_t nd = 0;
+    for (uint8_t x : c->dirty) nd += x;
+    o->dirty = nd;
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_ckpt_log(const phos_ckpt_t *c, uint32_t kind, uint64_t *out,
+                                     uint64_t cap, uint64_t *n_out) {
+    if (!c) return fail(PHOS_EINVAL, "ckpt_log: NULL session");
+    if (kind == 0) return copy_log(c->cow_log, out, cap, n_out);
+    if (kind == 1) return copy_log(c->ss.copier_log, out, cap, n_out);
+    if (kind == 2) {
+        std::vector<uint64_t> v;
+        for (uint32_t i = 0; i < c->ss.n; ++i)
+            if (c->dirty[i]) v.insert(v.end(), {i, 0, 0, 0, 0});
+        return copy_log(v, out, cap, n_out);
+    }
+    return fail(PHOS_EINVAL, "ckpt_log: kind %u", kind);
+}
+
+extern "C" phos_status phos_ckpt_end(phos_ckpt_t *c) {
+    delete c;
+    return PHOS_OK;
+}
+
+// ------------------------------------------------------------- restore
+
+struct phos_restore {
+    Session ss;
+    const void *image = nullptr;
+    uint64_t image_bytes = 0;
+    uint32_t *d_present = nullptr;
+    std::vector<uint8_t> present, before;
+    std::vector<uint64_t> od_log;
+    uint64_t copier_bytes = 0, ondemand_bytes = 0;
+    int64_t misspec = -1;
+    bool in_kernel = false;
+
+    bool all_present() const {
+        for (uint8_t p : present)
+            if (!p) return false;
+        return true;
+    }
+};
+
+extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_restore_desc_t *d,
+                                          phos_stream_t stream, phos_restore_t **out) {
+    if (!t || !d || !out) return fail(PHOS_EINVAL, "restore_begin: NULL argument");
+    *out = nullptr;
+    if (d->access_bytes == 0 || d->chunk == 0 || d->chunk % 256)
+        return fail(PHOS_EINVAL, "restore_begin: access_bytes >= 1, chunk a multiple of 256");
+    if (!d->image || d->image_bytes < t->image_bytes)
+        return fail(PHOS_EINVAL, "restore_begin: image smaller than %llu bytes",
+                    (unsigned long long)t->image_bytes);
+    phos_restore *r = new phos_restore();
+    phos_status e = r->ss.init(t, static_cast<cudaStream_t>(stream), d->access_bytes, d->chunk);
+    if (e) {
+        delete r;
+        return e;
+    }
+    r->image = d->image;
+    r->image_bytes = d->image_bytes;
+    r->d_present = d->d_present;
+    r->present.assign(t->n, 0);
+    r->before.assign(t->n, 0);
+    if (r->d_present && t->n) {
+        cudaError_t ce = cudaMemsetAsync(r->d_present, 0, 4ull * ((t->n + 31) / 32),
+                                         r->ss.s);
+        if (ce != cudaSuccess) {
+            delete r;
+            return cuda_fail(ce, "restore_begin: cudaMemsetAsync(present)");
+        }
+    }
+    *out = r;
+    return PHOS_OK;
+}
+
+static phos_status restore_advance(phos_restore *R, uint64_t quota) {
+    Session &S = R->ss;
+    const phos_table *t = S.t;
+    std::vector<phos_copy_t> v;
+    uint64_t moved = S.advance(
+        quota,
+        [&](uint32_t i, uint64_t off, uint64_t len) {
+            phos_copy_t d;
+            d.src_off = t->img_off[i] + off;
+            d.dst_off = off;
+            d.len = len;
+            d.buf = i;
+            d.flags = PHOS_COPY_IMAGE_TO_LIVE;
+            if (off + len == t->size[i]) {
+                R->present[i] = 1;
+                if (R->d_present) d.flags |= PHOS_COPY_MARK_PRESENT;
+            }
+            v.push_back(d);
+            return false;
+        },
+        [&](uint32_t i) { return R->present[i] != 0; });
+    R->copier_bytes += moved;
+    return S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
+}
+
+extern "C" phos_status phos_restore_advance(phos_restore_t *R, uint64_t quota, int *done) {
+    if (!R) return fail(PHOS_EINVAL, "restore_advance: NULL session");
+    if (R->in_kernel) return fail(PHOS_EINVAL, "restore_advance: inside a kernel round");
+    phos_status r = PHOS_OK;
+    if (!R->all_present()) r = restore_advance(R, quota);
+    if (done) *done = R->all_present() ? 1 : 0;
+    return r;
+}
+
+extern "C" phos_status phos_restore_before_kernel(phos_restore_t *R, const uint8_t *perm) {
+    if (!R) return fail(PHOS_EINVAL, "restore_before_kernel: NULL session");
+    if (R->in_kernel) return fail(PHOS_EINVAL, "restore_before_kernel: after_kernel missing");
+    Session &S = R->ss;
+    const phos_table *t = S.t;
+    phos_status r = S.stage_perm(perm);
+    if (r) return r;
+    std::vector<phos_copy_t> v;
+    for (uint32_t i = 0; i < S.n; ++i) {
+        if (!perm[i] || R->present[i]) continue;
+        const uint64_t cp = S.copied[i], sz = t->size[i];
+        phos_copy_t d;
+        d.src_off = t->img_off[i] + cp;
+        d.dst_off = cp;
+        d.len = sz - cp;
+        d.buf = i;
+        d.flags = PHOS_COPY_IMAGE_TO_LIVE | (R->d_present ? PHOS_COPY_MARK_PRESENT : 0);
+        v.push_back(d);
+        R->od_log.insert(R->od_log.end(), {S.round, i, cp, sz - cp, 0});
+        R->ondemand_bytes += sz - cp;
+        S.copied[i] = sz;
+        S.state[i] = kDone;
+        R->present[i] = 1;
+    }
+    R->before = R->present;
+    r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
+    if (r) return r;
+    R->in_kernel = true;
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_restore_after_kernel(phos_restore_t *R, const uint64_t *d_trace,
+                                                 uint64_t n_rec, int *misspec) {
+    if (!R) return fail(PHOS_EINVAL, "restore_after_kernel: NULL session");
+    if (!R->in_kernel) return fail(PHOS_EINVAL, "restore_after_kernel: before_kernel missing");
+    Session &S = R->ss;
+    R->in_kernel = false;
+    const uint64_t k = S.round++;
+    if (misspec) *misspec = 0;
+    phos_status r = S.validate_sync(d_trace, n_rec);
+    if (r) return r;
+    if (S.h_count[0] == S.h_count[2]) return PHOS_OK;  // only unmapped accesses
+    for (uint32_t i = 0; i < S.n; ++i) {
+        if (S.victim_bit(false, i) && !R->before[i]) {
+            // roll back: every buffer from the image, stop-the-world
+            R->misspec = (int64_t)k;
+            std::vector<phos_copy_t> v;
+            for (uint32_t j = 0; j < S.n; ++j) {
+                phos_copy_t d;
+                d.src_off = S.t->img_off[j];
+                d.dst_off = 0;
+                d.len = S.t->size[j];
+                d.buf = j;
+                d.flags = PHOS_COPY_IMAGE_TO_LIVE | (R->d_present ? PHOS_COPY_MARK_PRESENT : 0);
+                v.push_back(d);
+                R->present[j] = 1;
+                S.state[j] = kDone;
+                S.copied[j] = S.t->size[j];
+            }
+            r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
+            if (r) return r;
+            r = S.sync();
+            if (r) return r;
+            if (misspec) *misspec = 1;
+            return PHOS_OK;
+        }
+    }
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_restore_finish(phos_restore_t *R) {
+    if (!R) return fail(PHOS_EINVAL, "restore_finish: NULL session");
+    if (R->in_kernel) return fail(PHOS_EINVAL, "restore_finish: inside a kernel round");
+    if (!R->all_present()) {
+        phos_status r = restore_advance(R, ~0ull >> 2);
+        if (r) return r;
+    }
+    return R->ss.sync();
+}
+
+extern "C" phos_status phos_restore_stats(const phos_restore_t *R, phos_restore_stats_t *o) {
+    if (!R || !o) return fail(PHOS_EINVAL, "restore_stats: NULL argument");
+    memset(o, 0, sizeof *o);
+    o->kernels = R->ss.round;
+    o->copier_bytes = R->copier_bytes;
+    o->ondemand_bytes = R->ondemand_bytes;
+    o->validated = R->ss.validated;
+    o->violations = R->ss.violations;
+    o->misspec_round = R->misspec;
+    o->done = R->all_present() ? 1 : 0;
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_restore_log(const phos_restore_t *R, uint32_t kind, uint64_t *out,
+                                        uint64_t cap, uint64_t *n_out) {
+    if (!R) return fail(PHOS_EINVAL, "restore_log: NULL session");
+    if (kind == 0) return copy_log(R->od_log, out, cap, n_out);
+    if (kind == 1) return copy_log(R->ss.copier_log, out, cap, n_out);
+    return fail(PHOS_EINVAL, "restore_log: kind %u", kind);
+}
+
+extern "C" phos_status phos_restore_end(phos_restore_t *R) {
+    delete R;
+    return PHOS_OK;
+}

@@ -1,0 +1,480 @@
+// Access validation (PhoenixOS Sec. 4.1 "Runtime validation"; the read
+// check of Sec. 6): every recorded load/store address is looked up in the
+// sorted buffer table and checked against the permission speculated for
+// its buffer.
+//
+// B300 design
+//   * Persistent grid, one CTA per SM (148), each owning a contiguous range
+//     of 2048-record tiles (16 KiB).  Tiles stream HBM -> shared memory with
+//     one-dimensional bulk copies (TMA engine) into a ring of 2..6 stages,
+//     completion tracked by mbarriers: the only HBM traffic is the trace
+//     read once (8 B/record) plus the bitmap written once (1/8 B/record).
+//   * The table (base, size, two fence levels), the permission bytes and
+//     the victim bitmaps sit in shared memory when they fit (tables of up
+//     to ~9k buffers); larger tables are read through L1/L2.
+//   * Lookup is warp-cooperative: the 32 lanes of a warp hold 32
+//     consecutive records; one three-level 32-ary search (fence2 -> fence1
+//     -> base, one ballot per level, conflict-free smem reads) finds the
+//     interval of the warp's first valid record, every lane checks its own
+//     record against that interval, and only lanes that miss fall back to
+//     a private binary search.  Coalesced traces (a warp's 32 accesses in
+//     one buffer) therefore cost one search per 32 records.
+//   * Results: ballot -> one bitmap word per warp; popc -> per-warp counts;
+//     shared-memory atomics for victims; one last-block reduction writes
+//     the counts and victim bitmaps (overwriting the outputs, no memset).
+//   * The ascending index list is a second, optional launch: each CTA takes
+//     the exclusive prefix of the per-CTA violation counts and compacts its
+//     own bitmap words with a block scan, so the order is deterministic.
+#include <stdio.h>
+
+#include "internal.h"
+#include "ptx.cuh"
+
+namespace phos {
+
+constexpr uint32_t kTileRec = 2048;
+constexpr uint32_t kTileBytes = kTileRec * 8;
+constexpr uint32_t kValThreads = 1024;
+constexpr uint32_t kMaxStages = 8;
+constexpr uint64_t kRsvdMask = 0x3Full << 57;
+
+struct ValParams {
+    TableDev tab;
+    const uint8_t *perm;
+    const uint64_t *trace;
+    uint64_t n_rec;
+    uint64_t tiles;
+    uint32_t *bitmap;
+    uint64_t *count;
+    uint32_t *victim;
+    uint32_t *victim_st;
+    uint32_t *status;
+    // scratch
+    uint64_t *cta_cnt;  // [grid][4]
+    uint32_t *vacc;     // [2][nvw], zero between calls
+    uint32_t *ticket;   // zero between calls
+    uint32_t w;
+    uint32_t nvw;
+    uint32_t stages;
+};
+
+__device__ __forceinline__ int coop_search(uint64_t x, const uint64_t *base,
+                                           const uint64_t *f1, const uint64_t *f2, uint32_t n,
+                                           uint32_t lane) {
+    const uint64_t kMax = ~0ull;
+    uint32_t blk = 0;
+    if (n > 1024) {
+        const uint32_t nf2 = (n + 1023) >> 10;
+        uint64_t v = lane < nf2 ? f2[lane] : kMax;
+        uint32_t c = __popc(__ballot_sync(0xffffffffu, v <= x));
+        if (c == 0) return -1;
+        blk = c - 1;
+    }
+    if (n > 32) {
+        const uint32_t nf1 = (n + 31) >> 5;
+        uint32_t idx = blk * 32 + lane;
+        uint64_t v = idx < nf1 ? f1[idx] : kMax;
+        uint32_t c = __popc(__ballot_sync(0xffffffffu, v <= x));
+        if (c == 0) return -1;
+        blk = blk * 32 + c - 1;
+    }
+    uint32_t idx = blk * 32 + lane;
+    uint64_t v = idx < n ? base[idx] : kMax;
+    uint32_t c = __popc(__ballot_sync(0xffffffffu, v <= x));
+    if (c == 0) return -1;
+    return (int)(blk * 32 + c - 1);
+}
+
+__device__ __forceinline__ int lane_search(uint64_t a, const uint64_t *base, uint32_t n) {
+    uint32_t lo = 0, cnt = n;
+    while (cnt > 0) {
+        uint32_t half = cnt >> 1;
+        if (base[lo + half] <= a) {
+            lo += half + 1;
+            cnt -= half + 1;
+        } else {
+            cnt = half;
+        }
+    }
+    return (int)lo - 1;
+}
+
+__device__ __forceinline__ bool inside(uint64_t a, uint64_t b, uint64_t s, uint32_t w) {
+    return s >= w && (a - b) <= s - w;   // a < b wraps to a huge value
+}
+
+template <bool kSmemTable>
+__global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t S = p.stages, n = p.tab.n, nvw = p.nvw;
+    uint64_t *ring = reinterpret_cast<uint64_t *>(smem);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + (size_t)S * kTileBytes);
+    uint32_t *used = reinterpret_cast<uint32_t *>(mbar + kMaxStages);
+    uint32_t *issued = used + kMaxStages;
+    uint8_t *cur = reinterpret_cast<uint8_t *>(issued + kMaxStages);
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(cur);
+    uint32_t *flag = reinterpret_cast<uint32_t *>(cur + 24);
+    uint32_t *last = flag + 1;
+    cur += 32;
+    const uint32_t nf1 = (n + 31) >> 5, nf2 = (n + 1023) >> 10;
+    const uint64_t *base = p.tab.base, *size = p.tab.size, *f1 = p.tab.fence1,
+                   *f2 = p.tab.fence2;
+    if (kSmemTable) {
+        uint64_t *tb = reinterpret_cast<uint64_t *>(cur);
+        // base | size | fence1 | fence2 are contiguous in global memory
+        const uint64_t *g = p.tab.base;
+        const uint32_t words = 2 * n + nf1 + nf2;
+        for (uint32_t i = tid; i < words; i += blockDim.x) tb[i] = __ldg(g + i);
+        base = tb;
+        size = tb + n;
+        f1 = tb + 2 * n;
+        f2 = f1 + nf1;
+        cur += (size_t)words * 8;
+    }
+    uint8_t *perm = cur;
+    cur += (n + 15) & ~15u;
+    uint32_t *sv = reinterpret_cast<uint32_t *>(cur);
+    uint32_t *svs = sv + nvw;
+
+    for (uint32_t i = tid; i < n; i += blockDim.x) perm[i] = p.perm[i];
+    for (uint32_t i = tid; i < nvw; i += blockDim.x) sv[i] = svs[i] = 0;
+    if (tid == 0) {
+        for (uint32_t q = 0; q < S; ++q) {
+            mbar_init(&mbar[q], 1);
+            used[q] = 0;
+            issued[q] = ~0u;
+        }
+        fence_mbar_init();
+        red[0] = red[1] = red[2] = 0;
+        *flag = 0;
+    }
+    __syncthreads();
+
+    const uint64_t G = gridDim.x, c = blockIdx.x;
+    const uint64_t t0 = p.tiles * c / G, t1 = p.tiles * (c + 1) / G;
+    const uint32_t ntl = (uint32_t)(t1 - t0);
+
+    auto issue = [&](uint32_t j) {
+        const uint32_t s = j % S;
+        const uint64_t r0 = (t0 + j) * kTileRec;
+        const uint64_t cnt = min((uint64_t)kTileRec, p.n_rec - r0);
+        const uint32_t bytes = (uint32_t)(cnt * 8);
+        const uint32_t bulk = bytes & ~15u;
+        uint64_t *dst = ring + (size_t)s * kTileRec;
+        if (bytes & 8) dst[cnt - 1] = p.trace[r0 + cnt - 1];
+        mbar_arrive_expect_tx(&mbar[s], bulk);
+        if (bulk) bulk_g2s(dst, p.trace + r0, bulk, &mbar[s]);
+    };
+
+    if (tid == 0)
+        for (uint32_t j = 0; j < ntl && j < S; ++j) {
+            issued[j] = j;
+            issue(j);
+        }
+    __syncthreads();
+
+    // Every warp walks all of the CTA's tiles, taking words warp, warp+32,
+    // ... of each; warps run independently (no block barrier per tile).
+    // The last warp to finish a stage refills it with the tile S ahead.
+    uint64_t c0 = 0, c1 = 0, c2 = 0;
+    bool any_bad = false;
+    const uint32_t w = p.w;
+    uint32_t s = 0, par = 0;
+    uint64_t r0 = t0 * kTileRec;
+    for (uint32_t j = 0; j < ntl; ++j) {
+        if (!mbar_wait_bounded(&mbar[s], par)) {
+            if (lane == 0) atomicOr(flag, 1u);
+            break;
+        }
+        const uint32_t cnt = (uint32_t)min((uint64_t)kTileRec, p.n_rec - r0);
+        const uint32_t nw = (cnt + 31) >> 5;
+        const uint64_t *tile = ring + (size_t)s * kTileRec;
+        for (uint32_t wi = warp; wi < nw; wi += nwarps) {
+            const uint32_t rl = wi * 32 + lane;
+            const bool valid = rl < cnt;
+            const uint64_t rec = valid ? tile[rl] : 0ull;
+            const uint64_t a = rec & PHOS_REC_ADDR_MASK;
+            const bool st = (rec >> 63) != 0;
+            const bool bad = valid && (rec & kRsvdMask) != 0;
+            const bool cand = valid && !bad;
+            const uint32_t lm = __ballot_sync(0xffffffffu, cand);
+            bool hit = false;
+            int bi = -1;
+            if (lm) {
+                const uint32_t ld = (lm & 1u) ? 0u : (uint32_t)(__ffs(lm) - 1);
+                const uint64_t x = __shfl_sync(0xffffffffu, a, ld);
+                const int i0 = coop_search(x, base, f1, f2, n, lane);
+                if (i0 >= 0) {
+                    const uint64_t b0 = base[i0], s0 = size[i0];
+                    hit = cand && s0 >= w && (a - b0) <= s0 - w;
+                    bi = i0;
+                }
+                const bool miss = cand && !hit;
+                if (__ballot_sync(0xffffffffu, miss)) {
+                    if (miss) {
+                        const int ii = lane_search(a, base, n);
+                        if (ii >= 0 && inside(a, base[ii], size[ii], w)) {
+                            hit = true;
+                            bi = ii;
+                        }
+                    }
+                }
+            }
+            const uint8_t pm = hit ? perm[bi] : 0;
+            const bool viol = valid && (!hit || !(pm & (st ? 2 : 1)));
+            const uint32_t vw = __ballot_sync(0xffffffffu, viol);
+            if (lane == 0) p.bitmap[(r0 >> 5) + wi] = vw;
+            if (vw) {
+                const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
+                const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
+                if (lane == 0) {
+                    c0 += __popc(vw);
+                    c1 += __popc(sw);
+                    c2 += __popc(uw);
+                }
+                if (viol && hit) {
+                    atomicOr(&sv[bi >> 5], 1u << (bi & 31));
+                    if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
+                }
+                any_bad |= bad;
+            }
+        }
+        // release the stage; the last warp out refills it
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&used[s], 1u) == nwarps - 1) {
+                used[s] = 0;
+                const uint32_t nj = j + S;
+                if (nj < ntl) {
+                    issued[s] = nj;
+                    fence_proxy_async_smem();
+                    issue(nj);
+                } else {
+                    issued[s] = ~0u;
+                }
+            }
+        }
+        r0 += kTileRec;
+        if (++s == S) {
+            s = 0;
+            par ^= 1u;
+        }
+    }
+    __syncthreads();
+    if (*flag) {
+        // a bulk copy did not complete in time: wait (bounded) for what is
+        // still in flight before the CTA's shared memory is released
+        if (tid == 0) {
+            for (uint32_t q = 0; q < S; ++q)
+                if (issued[q] != ~0u)
+                    mbar_wait_bounded(&mbar[q], (issued[q] / S) & 1u);
+            set_status(p.status, PHOS_ETIMEDOUT);
+        }
+    }
+    if (__any_sync(0xffffffffu, any_bad) && lane == 0) set_status(p.status, PHOS_EINVAL);
+    if (lane == 0 && (c0 | c1 | c2)) {
+        atomicAdd(&red[0], (unsigned long long)c0);
+        atomicAdd(&red[1], (unsigned long long)c1);
+        atomicAdd(&red[2], (unsigned long long)c2);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        p.cta_cnt[c * 4 + 0] = red[0];
+        p.cta_cnt[c * 4 + 1] = red[1];
+        p.cta_cnt[c * 4 + 2] = red[2];
+    }
+    for (uint32_t i = tid; i < nvw; i += blockDim.x) {
+        if (sv[i]) atomicOr(&p.vacc[i], sv[i]);
+        if (svs[i]) atomicOr(&p.vacc[nvw + i], svs[i]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *last = (atomicAdd(p.ticket, 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
+    __syncthreads();
+    if (!*last) return;
+    // last CTA: every other CTA has published its partials
+    __threadfence();
+    if (tid == 0) red[0] = red[1] = red[2] = 0;
+    __syncthreads();
+    unsigned long long a0 = 0, a1 = 0, a2 = 0;
+    for (uint64_t q = tid; q < G; q += blockDim.x) {
+        a0 += __ldcg(p.cta_cnt + q * 4 + 0);
+        a1 += __ldcg(p.cta_cnt + q * 4 + 1);
+        a2 += __ldcg(p.cta_cnt + q * 4 + 2);
+    }
+    if (a0 | a1 | a2) {
+        atomicAdd(&red[0], a0);
+        atomicAdd(&red[1], a1);
+        atomicAdd(&red[2], a2);
+    }
+    for (uint32_t i = tid; i < nvw; i += blockDim.x) {
+        const uint32_t v = __ldcg(p.vacc + i), vs = __ldcg(p.vacc + nvw + i);
+        if (p.victim) p.victim[i] = v;
+        if (p.victim_st) p.victim_st[i] = vs;
+        p.vacc[i] = 0;
+        p.vacc[nvw + i] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        p.count[0] = red[0];
+        p.count[1] = red[1];
+        p.count[2] = red[2];
+        *p.ticket = 0;
+    }
+}
+
+// Ascending list of the first cap violating record indices.
+__global__ void __launch_bounds__(512) k_validate_emit(const uint32_t *bitmap, uint64_t n_rec,
+                                                       uint64_t tiles, const uint64_t *cta_cnt,
+                                                       uint64_t *idx, uint64_t cap) {
+    __shared__ unsigned long long s_pre;
+    __shared__ uint32_t s_warp[16];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t G = gridDim.x, c = blockIdx.x;
+    if (cta_cnt[c * 4] == 0) return;
+    if (tid == 0) s_pre = 0;
+    __syncthreads();
+    unsigned long long pre = 0;
+    for (uint64_t q = tid; q < c; q += blockDim.x) pre += cta_cnt[q * 4];
+    if (pre) atomicAdd(&s_pre, pre);
+    __syncthreads();
+    uint64_t prefix = s_pre;
+    if (prefix >= cap) return;
+    const uint64_t t0 = tiles * c / G, t1 = tiles * (c + 1) / G;
+    const uint64_t nwords = (n_rec + 31) / 32;
+    const uint64_t w0 = t0 * (kTileRec / 32), w1 = min(t1 * (kTileRec / 32), nwords);
+    for (uint64_t wb = w0; wb < w1; wb += blockDim.x) {
+        const uint64_t wi = wb + tid;
+        uint32_t v = wi < w1 ? bitmap[wi] : 0u;
+        uint32_t pc = __popc(v);
+        // block exclusive scan of pc
+        uint32_t incl = pc;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t woff = 0, total = 0;
+        for (uint32_t q = 0; q < (blockDim.x >> 5); ++q) {
+            if (q < warp) woff += s_warp[q];
+            total += s_warp[q];
+        }
+        uint64_t pos = prefix + woff + incl - pc;
+        while (v && pos < cap) {
+            const uint32_t b = __ffs(v) - 1;
+            idx[pos++] = wi * 32 + b;
+            v &= v - 1;
+        }
+        prefix += total;
+        __syncthreads();
+        if (prefix >= cap) break;
+    }
+}
+
+struct ValPlan {
+    bool smem_table;
+    uint32_t stages;
+    size_t smem;
+};
+
+static ValPlan plan_validate(uint32_t n, int device) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (optin <= 0) optin = 227 * 1024;
+    const uint32_t nvw = (n + 31) / 32, nf1 = (n + 31) / 32, nf2 = (n + 1023) / 1024;
+    const size_t fixed = 32 + ((n + 15) & ~15u) + 8ull * nvw;
+    const size_t tab = 8ull * (2 * n + nf1 + nf2);
+    const size_t ctl = 16ull * kMaxStages;   // mbarriers, used[], issued[]
+    for (uint32_t S = kMaxStages; S >= 2; --S) {
+        size_t need = (size_t)S * kTileBytes + ctl + fixed + tab;
+        if (need <= (size_t)optin) return {true, S, need};
+    }
+    uint32_t S = 6;
+    size_t need = (size_t)S * kTileBytes + ctl + fixed;
+    return {false, S, need};
+}
+
+}  // namespace phos
+
+using namespace phos;
+
+extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
+                                     const uint64_t *d_trace, uint64_t n_rec,
+                                     uint32_t access_bytes, uint32_t *d_bitmap,
+                                     uint64_t *d_count, uint32_t *d_victim,
+                                     uint32_t *d_victim_st, uint64_t *d_idx, uint64_t idx_cap,
+                                     uint32_t *d_status, phos_stream_t stream) {
+    if (!t) return fail(PHOS_EINVAL, "validate: table is NULL");
+    if (!d_count) return fail(PHOS_EINVAL, "validate: d_count is NULL");
+    if (access_bytes == 0) return fail(PHOS_EINVAL, "validate: access_bytes is 0");
+    if (n_rec && (!d_trace || !d_bitmap))
+        return fail(PHOS_EINVAL, "validate: NULL trace or bitmap");
+    if (n_rec && ((uintptr_t)d_trace & 15))
+        return fail(PHOS_EINVAL, "validate: trace must be 16-byte aligned");
+    if (t->n && !d_perm) return fail(PHOS_EINVAL, "validate: d_perm is NULL");
+    if (idx_cap && !d_idx) return fail(PHOS_EINVAL, "validate: idx_cap > 0 with NULL d_idx");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    phos_table *T = const_cast<phos_table *>(t);
+    const uint64_t tiles = (n_rec + kTileRec - 1) / kTileRec;
+    const int sms = sm_count(T->device);
+    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms, tiles));
+    const uint32_t nvw = (t->n + 31) / 32;
+    const size_t off_vacc = 256, off_cnt = align_up(off_vacc + 8ull * std::max(nvw, 1u), 256);
+    const size_t need = off_cnt + 32ull * (size_t)sms;
+    {
+        std::lock_guard<std::mutex> g(T->mu);
+        phos_status r = T->val_scratch.reserve(need);
+        if (r) return r;
+    }
+    uint8_t *sc = static_cast<uint8_t *>(T->val_scratch.ptr);
+    ValParams p;
+    p.tab = t->view;
+    p.perm = d_perm;
+    p.trace = d_trace;
+    p.n_rec = n_rec;
+    p.tiles = tiles;
+    p.bitmap = d_bitmap;
+    p.count = d_count;
+    p.victim = d_victim;
+    p.victim_st = d_victim_st;
+    p.status = d_status;
+    p.ticket = reinterpret_cast<uint32_t *>(sc);
+    p.vacc = reinterpret_cast<uint32_t *>(sc + off_vacc);
+    p.cta_cnt = reinterpret_cast<uint64_t *>(sc + off_cnt);
+    p.w = access_bytes;
+    p.nvw = nvw;
+    ValPlan pl = plan_validate(t->n, T->device);
+    p.stages = pl.stages;
+    static bool attr_done[2] = {false, false};
+    if (pl.smem_table) {
+        if (!attr_done[0]) {
+            PHOS_CUDA(cudaFuncSetAttribute(k_validate<true>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           227 * 1024));
+            attr_done[0] = true;
+        }
+        k_validate<true><<<(unsigned)G, kValThreads, pl.smem, s>>>(p);
+        count_launch();
+    } else {
+        if (!attr_done[1]) {
+            PHOS_CUDA(cudaFuncSetAttribute(k_validate<false>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           227 * 1024));
+            attr_done[1] = true;
+        }
+        k_validate<false><<<(unsigned)G, kValThreads, pl.smem, s>>>(p);
+        count_launch();
+    }
+    PHOS_CUDA(cudaGetLastError());
+    if (d_idx && idx_cap && n_rec) {
+        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, tiles, p.cta_cnt, d_idx,
+                                                    idx_cap);
+        count_launch();
+        PHOS_CUDA(cudaGetLastError());
+    }
+    return PHOS_OK;
+}

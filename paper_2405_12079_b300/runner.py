@@ -1,0 +1,128 @@
+"""Lockstep drivers that play the application around the C/R sessions.
+
+A ``DeviceProcess`` is one GPU process image: a device arena holding every
+buffer, the buffer table, and a sequence of application kernels (the
+harness mutator, launch arguments for speculation, access traces resident
+in HBM).  ``run_cow`` / ``run_recopy`` / ``run_restore`` perform one
+concurrent checkpoint or restore through the library's control plane in
+the round order its header defines: copier advance, speculation +
+before_kernel, the application kernel, after_kernel (validation).  All data
+movement and validation happen in libphos.so; this module only sequences
+the calls.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import phos
+
+
+class PreparedKernel:
+    """A kernel with its launch arguments marshalled once for speculation
+    and its trace and stray list resident on the device."""
+
+    def __init__(self, kern, device="cuda"):
+        self.kern = kern
+        self.nargs = len(kern.args)
+        self._bufs = [ctypes.create_string_buffer(bytes(a), max(len(a), 1)) for a in kern.args]
+        self.argv = (ctypes.c_void_p * max(self.nargs, 1))(
+            *[ctypes.cast(b, ctypes.c_void_p) for b in self._bufs])
+        self.asz = np.array([len(a) for a in kern.args] or [0], np.uint32)
+        self.kinds = np.array(list(kern.kinds) or [0], np.uint8)
+        tr = np.ascontiguousarray(kern.trace, np.uint64)
+        self.n_rec = len(tr)
+        self.d_trace = torch.from_numpy((tr if len(tr) else np.zeros(2, np.uint64))
+                                        .view(np.uint8).copy()).to(device)
+        self.reads = np.ascontiguousarray(kern.reads, np.uint32)
+        self.writes = np.ascontiguousarray(kern.writes, np.uint32)
+        st = np.array(kern.strays, np.uint64).reshape(-1) if kern.strays else np.zeros(2,
+                                                                                       np.uint64)
+        self.ns = len(kern.strays)
+        self.d_strays = torch.from_numpy(st.view(np.uint8).copy()).to(device)
+
+    def speculate(self, table, out):
+        out[:] = 0
+        phos.check(phos.lib().phos_speculate(table.handle, self.argv, self.asz.ctypes.data,
+                                             self.kinds.ctypes.data, self.nargs,
+                                             out.ctypes.data), "speculate")
+        return out
+
+
+class DeviceProcess:
+    def __init__(self, layout, arena, seed, kernels):
+        """arena: CUDA uint8 tensor of layout.arena_bytes (the process's
+        memory); kernels: workloads.Kernel list whose addresses are based at
+        arena.data_ptr()."""
+        self.layout = layout
+        self.arena = arena
+        self.va0 = arena.data_ptr()
+        self.seed = int(seed)
+        self.table = phos.Table(layout.base(self.va0), layout.size)
+        self.kernels = [PreparedKernel(k, arena.device) for k in kernels]
+        self.perm = np.zeros(max(layout.n, 1), np.uint8)
+        self.image_bytes = self.table.image_bytes()
+        self.img_off = self.table.image_offsets()
+
+    def stream(self):
+        return torch.cuda.current_stream().cuda_stream
+
+    def run_kernel(self, k):
+        pk = self.kernels[k]
+        phos.harness_mutate(self.table, self.seed, k, pk.reads, pk.writes,
+                            pk.d_strays.data_ptr(), pk.ns, self.stream())
+
+    def run_cow(self, image, quota, chunk, staging=None, staging_bytes=0):
+        return self._ckpt(phos.CKPT_COW, image, quota, chunk, staging, staging_bytes)
+
+    def run_recopy(self, image, quota, chunk):
+        return self._ckpt(phos.CKPT_RECOPY, image, quota, chunk, None, 0)
+
+    def _ckpt(self, mode, image, quota, chunk, staging, staging_bytes):
+        s = self.stream()
+        c = phos.Checkpoint(self.table, mode, image.data_ptr(), image.numel(), chunk, 4,
+                            staging.data_ptr() if staging is not None else None, staging_bytes, s)
+        k, misspec = 0, False
+        K = len(self.kernels)
+        while k < K:
+            if c.advance(quota):
+                break
+            pk = self.kernels[k]
+            c.before_kernel(pk.speculate(self.table, self.perm))
+            self.run_kernel(k)
+            misspec = c.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
+            k += 1
+            if misspec:
+                break
+        c.finish()
+        out = dict(stats=c.stats(), cow=c.log(0), copier=c.log(1), dirty=c.log(2)[:, 0],
+                   kernels_run=k)
+        c.close()
+        return out
+
+    def run_restore(self, image, quota, chunk, d_present=None):
+        """Concurrent restore followed by the rest of the kernels."""
+        s = self.stream()
+        r = phos.Restore(self.table, image.data_ptr(), image.numel(), chunk, 4,
+                         d_present.data_ptr() if d_present is not None else None, s)
+        k = 0
+        K = len(self.kernels)
+        while k < K:
+            if r.advance(quota):
+                break
+            pk = self.kernels[k]
+            r.before_kernel(pk.speculate(self.table, self.perm))
+            self.run_kernel(k)
+            misspec = r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
+            k += 1
+            if misspec:
+                for j in range(k):          # roll back happened: replay
+                    self.run_kernel(j)
+                break
+        r.finish()
+        during = k
+        for j in range(k, K):
+            self.run_kernel(j)
+        out = dict(stats=r.stats(), ondemand=r.log(0), copier=r.log(1), kernels_during=during)
+        r.close()
+        return out

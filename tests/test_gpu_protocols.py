@@ -1,0 +1,176 @@
+"""GPU parity of the lockstep protocol drivers against the oracle: soft
+copy-on-write (Sec. 4.2), soft recopy (Sec. 4.3) and soft on-demand restore
+(Sec. 6) produce exactly the oracle's CoW lists, copier pieces, dirty sets,
+on-demand lists, fallback rounds, checkpoint image and final memory, on
+scaled training-process, tiny and large-restore workloads and on
+mis-speculation scenarios."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import protocols as P  # noqa: E402
+from paper_2405_12079_b300 import phos, runner, workloads as wl  # noqa: E402
+
+
+def a256(x):
+    return (int(x) + 255) // 256 * 256
+
+
+class World:
+    def __init__(self, layout, seed, make_kernels):
+        self.lay = layout
+        rng = np.random.default_rng(seed)
+        self.mem0 = np.zeros(layout.arena_bytes, np.uint8)
+        wl.fill_random(rng, self.mem0)
+        self.arena = torch.from_numpy(self.mem0.copy()).cuda()
+        self.va0 = self.arena.data_ptr()
+        self.kernels = make_kernels(rng, layout, self.va0)
+        self.seed = seed
+        self.dp = runner.DeviceProcess(layout, self.arena, seed, self.kernels)
+
+    def oracle_proc(self, mem=None):
+        m = self.mem0.copy() if mem is None else mem
+        return P.Process(self.va0, self.lay.off, self.lay.size, m, self.seed)
+
+    def live_equal(self, proc):
+        return np.array_equal(self.arena.cpu().numpy(), proc.mem)
+
+
+def cow_rows(log):
+    return [(int(k), int(i), 1 if kind == "S" else 2, int(o), int(ln))
+            for k, i, kind, o, ln in log]
+
+
+def copier_rows(log):
+    return [(int(r), int(i), int(o), int(ln), int(bool(sh))) for r, i, o, ln, sh in log]
+
+
+def training_world(seed, scale, n_kernels, stray_store_frac=0.0):
+    cfg = wl.training(scale=scale, seed=seed, n_kernels=n_kernels)
+
+    def mk(rng, lay, va0):
+        return wl.make_training_kernels(rng, lay, va0, n_kernels, cfg["n_rec"], 0.001,
+                                        stray_store_frac)
+    return World(cfg["layout"], seed, mk), cfg
+
+
+def check_ckpt(w, mode, quota, chunk, staging_bytes=0):
+    img = torch.zeros(w.dp.image_bytes, dtype=torch.uint8).pin_memory()
+    stg = torch.zeros(max(staging_bytes, 256), dtype=torch.uint8, device="cuda")
+    proc = w.oracle_proc()
+    if mode == "cow":
+        exp = P.cow_checkpoint(proc, w.kernels, staging_bytes, chunk, quota)
+        got = w.dp.run_cow(img, quota, chunk, stg, staging_bytes)
+        assert got["stats"]["misspec_round"] == (-1 if exp.misspec is None else exp.misspec)
+        assert [tuple(int(x) for x in r) for r in got["cow"]] == cow_rows(exp.cow_log)
+        assert got["stats"]["cow_bytes"] == exp.stats["cow_bytes"]
+        assert got["stats"]["direct_bytes"] == exp.stats["direct_bytes"]
+    else:
+        exp = P.recopy_checkpoint(proc, w.kernels, chunk, quota)
+        got = w.dp.run_recopy(img, quota, chunk)
+        assert got["dirty"].tolist() == exp.dirty
+        assert got["stats"]["recopy_bytes"] == exp.stats["recopy_bytes"]
+    torch.cuda.synchronize()
+    assert got["kernels_run"] == exp.kernels_run
+    assert [tuple(int(x) for x in r) for r in got["copier"]] == copier_rows(exp.copier_log)
+    assert np.array_equal(img.numpy(), exp.image)
+    assert w.live_equal(proc)
+    return got, exp
+
+
+@pytest.mark.parametrize("mode", ["cow", "recopy"])
+def test_training_image_scaled(mode):
+    """Training-process shape at 1/500 scale (1,000 buffers, ~80 MB,
+    200 kernels); quota = image/100, chunk 64 KiB, staging 4 MB."""
+    w, cfg = training_world(wl.SEED0 + 2, 0.002, 200)
+    quota = a256(w.dp.image_bytes / 100)
+    got, exp = check_ckpt(w, mode, quota, 64 * 1024, staging_bytes=4 << 20)
+    if mode == "cow":
+        assert len(exp.cow_log) > 0 and exp.misspec is None
+    else:
+        assert len(exp.dirty) > 0
+
+
+@pytest.mark.parametrize("mode", ["cow", "recopy"])
+def test_stray_stores_fault_injection(mode):
+    """1 % of strays are stores outside the speculation: CoW falls back to
+    stop-the-world, recopy adds the victims to the dirty set."""
+    w, cfg = training_world(wl.SEED0 + 12, 0.001, 80, stray_store_frac=0.3)
+    quota = a256(w.dp.image_bytes / 60)
+    got, exp = check_ckpt(w, mode, quota, 32 * 1024, staging_bytes=1 << 20)
+    if mode == "cow":
+        assert exp.misspec is not None
+
+
+def test_cow_budget_zero_and_tiny_config():
+    """Tiny config: 64 buffers, write set of 16, 1M-record random trace
+    with 3 % other-buffer accesses (stores among them force the fallback);
+    and a zero staging budget (every CoW goes straight to the image)."""
+    cfg = wl.tiny()
+    lay = cfg["layout"]
+    wset = cfg["wset"]
+
+    def mk(rng, lay_, va0):
+        rec, cls = wl.trace_random(rng, lay_, va0, wset, cfg["n_rec"])
+        args, kinds = wl.make_args(rng, lay_, va0, wset, wset)
+        return [wl.Kernel(args, kinds, wset, wset, rec, cls, 4, [])]
+    w = World(lay, cfg["seed"], mk)
+    check_ckpt(w, "cow", a256(w.dp.image_bytes / 4), 1 << 16, staging_bytes=64 << 20)
+
+    def mk2(rng, lay_, va0):
+        ks = []
+        for _ in range(12):
+            r, wr = wl.pick_sets(rng, lay_.n, 1, 8)
+            args, kinds = wl.make_args(rng, lay_, va0, r, wr)
+            rec, cls, st = wl.trace_runs(rng, lay_, va0, r, wr, 4096, 0.0)
+            ks.append(wl.Kernel(args, kinds, r, wr, rec, cls, 4, st))
+        return ks
+    w2 = World(lay, cfg["seed"] + 100, mk2)
+    got, exp = check_ckpt(w2, "cow", a256(w2.dp.image_bytes / 20), 1 << 16, staging_bytes=0)
+    assert all(e[2] == "D" for e in exp.cow_log)
+
+
+def check_restore(w, quota, chunk):
+    proc = w.oracle_proc()
+    image = P.stw_checkpoint(proc)
+    img = torch.from_numpy(image.copy()).pin_memory()
+    # the restored process starts from memory that is not the checkpoint
+    w.arena.fill_(0xA5)
+    cur = w.oracle_proc(np.full(w.lay.arena_bytes, 0xA5, np.uint8))
+    exp = P.concurrent_restore(cur, image, w.kernels, chunk, quota)
+    present = torch.zeros(4 * ((w.lay.n + 31) // 32), dtype=torch.uint8, device="cuda")
+    got = w.dp.run_restore(img, quota, chunk, present)
+    torch.cuda.synchronize()
+    assert got["stats"]["misspec_round"] == (-1 if exp.misspec is None else exp.misspec)
+    assert got["kernels_during"] == exp.kernels_during
+    assert [tuple(int(x) for x in r) for r in got["ondemand"]] == \
+        [(int(k), int(i), int(o), int(ln), 0) for k, i, o, ln in exp.ondemand]
+    assert [tuple(int(x) for x in r) for r in got["copier"]] == copier_rows(exp.copier_log)
+    assert w.live_equal(cur)
+    bits = present.cpu().numpy().view(np.uint32)
+    assert int(sum(bin(int(x)).count("1") for x in bits)) == w.lay.n
+    return got, exp
+
+
+def test_large_restore_scaled():
+    """Large-restore shape at small scale: 10,000 buffers, layer-local
+    read/write sets, background bulk restore plus on-demand copies."""
+    cfg = wl.large_restore(scale=0.0005, n_kernels=150, n_rec=1024)
+
+    def mk(rng, lay, va0):
+        return wl.make_restore_kernels(rng, lay, va0, cfg["n_kernels"], cfg["n_rec"])
+    w = World(cfg["layout"], cfg["seed"], mk)
+    got, exp = check_restore(w, a256(w.dp.image_bytes / 300), 64 * 1024)
+    assert len(exp.ondemand) > 0
+
+
+def test_restore_stray_load_rolls_back():
+    cfg = wl.training(scale=0.0005, seed=wl.SEED0 + 22, n_kernels=40)
+
+    def mk(rng, lay, va0):
+        return wl.make_training_kernels(rng, lay, va0, 40, cfg["n_rec"], stray_frac=0.002)
+    w = World(cfg["layout"], cfg["seed"], mk)
+    got, exp = check_restore(w, a256(w.dp.image_bytes / 80), 32 * 1024)
+    assert exp.misspec is not None
