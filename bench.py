@@ -72,7 +72,7 @@ def oracle_sample(scale, n_kernels=200, seed=None):
     return moved, recs, dt
 
 
-def cpu_baseline(scale=0.005):
+def cpu_baseline(scale=0.04):
     moved, recs, dt = oracle_sample(scale)
     return {"value": moved / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": "oracle CoW + recopy checkpoint of the same workload scaled to %.1f%% "
@@ -83,7 +83,7 @@ def cpu_baseline(scale=0.005):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    scale = 0.002
+    scale = 0.01
     for _ in range(args.warmup):
         oracle_sample(scale)
     tot_b, tot_t = 0, 0.0

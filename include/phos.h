@@ -160,6 +160,13 @@ phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
                           uint32_t *d_victim_st, uint64_t *d_idx, uint64_t idx_cap,
                           uint32_t *d_status, phos_stream_t stream);
 
+/* Kernel variant of phos_validate (process-wide; the autotuner sets it):
+ * 0 = default, 1 = bulk-copy ring with one warp-cooperative search per
+ * 32 records, 2 = batched leaders (each lane searches the first record of
+ * one of 32 words, the warp checks all 32 words against them).  Results
+ * are identical; only speed differs. */
+phos_status phos_validate_config(uint32_t variant);
+
 /* --------------------------------------------------------- copy engine */
 
 /* Gather-copy n descriptors (d_list: device array) between live buffers,

@@ -9,16 +9,20 @@
 //     one-dimensional bulk copies (TMA engine) into a ring of 2..6 stages,
 //     completion tracked by mbarriers: the only HBM traffic is the trace
 //     read once (8 B/record) plus the bitmap written once (1/8 B/record).
-//   * The table (base, size, two fence levels), the permission bytes and
-//     the victim bitmaps sit in shared memory when they fit (tables of up
-//     to ~9k buffers); larger tables are read through L1/L2.
+//   * The table (base, per-call access limit, two fence levels), the
+//     permission bytes and the victim bitmaps sit in shared memory when
+//     they fit (tables of up to ~11k buffers); larger tables are read
+//     through L1/L2.
 //   * Lookup is warp-cooperative: the 32 lanes of a warp hold 32
-//     consecutive records; one three-level 32-ary search (fence2 -> fence1
-//     -> base, one ballot per level, conflict-free smem reads) finds the
-//     interval of the warp's first valid record, every lane checks its own
-//     record against that interval, and only lanes that miss fall back to
-//     a private binary search.  Coalesced traces (a warp's 32 accesses in
-//     one buffer) therefore cost one search per 32 records.
+//     consecutive records; one 32-ary search (top level held in registers,
+//     then fence1 and base in shared memory, one ballot per level,
+//     conflict-free reads) finds the interval of lane 0's record, every
+//     lane checks its own record against that interval with one unsigned
+//     compare, and only lanes that miss fall back to a private binary
+//     search.  Coalesced traces (a warp's 32 accesses in one buffer)
+//     therefore cost one search per 32 records.
+//   * Stages are released per warp: the last warp to finish a stage
+//     refills it, so warps never wait for each other inside the loop.
 //   * Results: ballot -> one bitmap word per warp; popc -> per-warp counts;
 //     shared-memory atomics for victims; one last-block reduction writes
 //     the counts and victim bitmaps (overwriting the outputs, no memset).
@@ -58,49 +62,117 @@ struct ValParams {
     uint32_t stages;
 };
 
-__device__ __forceinline__ int coop_search(uint64_t x, const uint64_t *base,
-                                           const uint64_t *f1, const uint64_t *f2, uint32_t n,
-                                           uint32_t lane) {
-    const uint64_t kMax = ~0ull;
-    uint32_t blk = 0;
-    if (n > 1024) {
-        const uint32_t nf2 = (n + 1023) >> 10;
-        uint64_t v = lane < nf2 ? f2[lane] : kMax;
-        uint32_t c = __popc(__ballot_sync(0xffffffffu, v <= x));
-        if (c == 0) return -1;
-        blk = c - 1;
-    }
-    if (n > 32) {
-        const uint32_t nf1 = (n + 31) >> 5;
-        uint32_t idx = blk * 32 + lane;
-        uint64_t v = idx < nf1 ? f1[idx] : kMax;
-        uint32_t c = __popc(__ballot_sync(0xffffffffu, v <= x));
-        if (c == 0) return -1;
-        blk = blk * 32 + c - 1;
-    }
-    uint32_t idx = blk * 32 + lane;
-    uint64_t v = idx < n ? base[idx] : kMax;
-    uint32_t c = __popc(__ballot_sync(0xffffffffu, v <= x));
-    if (c == 0) return -1;
-    return (int)(blk * 32 + c - 1);
-}
+// Table view used by the lookup.  lim[i] = number of valid start offsets
+// of a w-byte access in buffer i (size - w + 1, or 0 if size < w), so that
+// [a, a+w) lies in buffer i  <=>  a - base[i] < lim[i]  (unsigned; a below
+// base wraps to a huge value).
+struct Look {
+    const uint64_t *base;
+    const uint64_t *lim;     // shared-memory path
+    const uint64_t *size;    // global path: lim computed on the fly
+    const uint64_t *f1;
+    const uint64_t *f2;
+    const uint8_t *perm;
+    uint32_t n, nf1, w;
+    uint64_t rf;             // this lane's entry of the top search level
 
-__device__ __forceinline__ int lane_search(uint64_t a, const uint64_t *base, uint32_t n) {
-    uint32_t lo = 0, cnt = n;
-    while (cnt > 0) {
-        uint32_t half = cnt >> 1;
-        if (base[lo + half] <= a) {
-            lo += half + 1;
-            cnt -= half + 1;
-        } else {
-            cnt = half;
+    __device__ __forceinline__ uint64_t limit(int i, bool smem_lim) const {
+        if (smem_lim) return lim[i];
+        const uint64_t s = size[i];
+        return s >= w ? s - w + 1 : 0;
+    }
+
+    // Warp-uniform x: index of the last buffer with base <= x, or -1.
+    // One ballot per level; the top level lives in registers.
+    __device__ __forceinline__ int search(uint64_t x, uint32_t lane) const {
+        const uint64_t kMax = ~0ull;
+        uint32_t c = __popc(__ballot_sync(0xffffffffu, rf <= x));
+        if (n <= 32) return (int)c - 1;
+        if (c == 0) return -1;
+        uint32_t blk = c - 1;
+        if (n > 1024) {
+            const uint32_t idx = blk * 32 + lane;
+            const uint64_t v = idx < nf1 ? f1[idx] : kMax;
+            blk = blk * 32 + __popc(__ballot_sync(0xffffffffu, v <= x)) - 1;
+        }
+        const uint32_t idx = blk * 32 + lane;
+        const uint64_t v = idx < n ? base[idx] : kMax;
+        return (int)(blk * 32 + __popc(__ballot_sync(0xffffffffu, v <= x)) - 1);
+    }
+
+    // Per-lane binary search (divergent fallback).
+    __device__ __forceinline__ int lane_search(uint64_t a) const {
+        uint32_t lo = 0, cnt = n;
+        while (cnt > 0) {
+            const uint32_t half = cnt >> 1;
+            if (base[lo + half] <= a) {
+                lo += half + 1;
+                cnt -= half + 1;
+            } else {
+                cnt = half;
+            }
+        }
+        return (int)lo - 1;
+    }
+};
+
+struct Acc {
+    uint64_t c0 = 0, c1 = 0, c2 = 0;
+    bool bad = false;
+};
+
+// Classify the 32 records of one bitmap word (one per lane) and write the
+// word.  kFull: every lane holds a record.
+template <bool kFull, bool kSmemLim>
+__device__ __forceinline__ void word(const Look &L, uint64_t rec, bool valid, uint32_t lane,
+                                     uint32_t *bm_word, uint32_t *sv, uint32_t *svs, Acc &acc) {
+    if (kFull) valid = true;
+    const uint64_t a = rec & PHOS_REC_ADDR_MASK;
+    const uint32_t hi = (uint32_t)(rec >> 32);
+    const bool st = (int32_t)hi < 0;
+    const bool bad = (hi & 0x7E000000u) != 0;
+    // leader: lane 0's address (any choice is correct; lanes that miss fall
+    // back to their own search)
+    const uint64_t x = __shfl_sync(0xffffffffu, a, 0);
+    const int i0 = L.search(x, lane);
+    int bi = i0;
+    uint32_t pm = 0;
+    bool hit = false;
+    if (i0 >= 0) {
+        const uint64_t b0 = L.base[i0];
+        const uint64_t l0 = L.limit(i0, kSmemLim);
+        pm = L.perm[i0];
+        hit = (a - b0) < l0;
+    }
+    hit = hit && !bad && valid;
+    const bool miss = valid && !bad && !hit;
+    if (__ballot_sync(0xffffffffu, miss)) {
+        if (miss) {
+            const int ii = L.lane_search(a);
+            if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemLim)) {
+                hit = true;
+                bi = ii;
+                pm = L.perm[ii];
+            }
         }
     }
-    return (int)lo - 1;
-}
-
-__device__ __forceinline__ bool inside(uint64_t a, uint64_t b, uint64_t s, uint32_t w) {
-    return s >= w && (a - b) <= s - w;   // a < b wraps to a huge value
+    const bool viol = valid && !(hit && (pm & (st ? 2u : 1u)));
+    const uint32_t vw = __ballot_sync(0xffffffffu, viol);
+    if (lane == 0) *bm_word = vw;
+    if (vw) {
+        const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
+        const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
+        if (lane == 0) {
+            acc.c0 += __popc(vw);
+            acc.c1 += __popc(sw);
+            acc.c2 += __popc(uw);
+        }
+        if (viol && hit) {
+            atomicOr(&sv[bi >> 5], 1u << (bi & 31));
+            if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
+        }
+        acc.bad |= bad;
+    }
 }
 
 template <bool kSmemTable>
@@ -119,24 +191,37 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
     uint32_t *last = flag + 1;
     cur += 32;
     const uint32_t nf1 = (n + 31) >> 5, nf2 = (n + 1023) >> 10;
-    const uint64_t *base = p.tab.base, *size = p.tab.size, *f1 = p.tab.fence1,
-                   *f2 = p.tab.fence2;
+    Look L;
+    L.n = n;
+    L.nf1 = nf1;
+    L.w = p.w;
+    L.base = p.tab.base;
+    L.size = p.tab.size;
+    L.lim = nullptr;
+    L.f1 = p.tab.fence1;
+    L.f2 = p.tab.fence2;
     if (kSmemTable) {
         uint64_t *tb = reinterpret_cast<uint64_t *>(cur);
-        // base | size | fence1 | fence2 are contiguous in global memory
-        const uint64_t *g = p.tab.base;
-        const uint32_t words = 2 * n + nf1 + nf2;
-        for (uint32_t i = tid; i < words; i += blockDim.x) tb[i] = __ldg(g + i);
-        base = tb;
-        size = tb + n;
-        f1 = tb + 2 * n;
-        f2 = f1 + nf1;
-        cur += (size_t)words * 8;
+        uint64_t *tl = tb + n, *t1 = tl + n, *t2 = t1 + nf1;
+        const uint32_t w = p.w;
+        for (uint32_t i = tid; i < n; i += blockDim.x) {
+            tb[i] = __ldg(p.tab.base + i);
+            const uint64_t sz = __ldg(p.tab.size + i);
+            tl[i] = sz >= w ? sz - w + 1 : 0;
+        }
+        for (uint32_t i = tid; i < nf1; i += blockDim.x) t1[i] = __ldg(p.tab.fence1 + i);
+        for (uint32_t i = tid; i < nf2; i += blockDim.x) t2[i] = __ldg(p.tab.fence2 + i);
+        L.base = tb;
+        L.lim = tl;
+        L.f1 = t1;
+        L.f2 = t2;
+        cur += 8ull * (2 * n + nf1 + nf2);
     }
     uint8_t *perm = cur;
     cur += (n + 15) & ~15u;
     uint32_t *sv = reinterpret_cast<uint32_t *>(cur);
     uint32_t *svs = sv + nvw;
+    L.perm = perm;
 
     for (uint32_t i = tid; i < n; i += blockDim.x) perm[i] = p.perm[i];
     for (uint32_t i = tid; i < nvw; i += blockDim.x) sv[i] = svs[i] = 0;
@@ -151,6 +236,17 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
         *flag = 0;
     }
     __syncthreads();
+    // top search level in registers: base (n <= 32), fence1 (n <= 1024) or
+    // fence2 (larger tables), one entry per lane
+    {
+        const uint64_t kMax = ~0ull;
+        if (n <= 32)
+            L.rf = lane < n ? L.base[lane] : kMax;
+        else if (n <= 1024)
+            L.rf = lane < nf1 ? L.f1[lane] : kMax;
+        else
+            L.rf = lane < nf2 ? L.f2[lane] : kMax;
+    }
 
     const uint64_t G = gridDim.x, c = blockIdx.x;
     const uint64_t t0 = p.tiles * c / G, t1 = p.tiles * (c + 1) / G;
@@ -175,12 +271,11 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
         }
     __syncthreads();
 
-    // Every warp walks all of the CTA's tiles, taking words warp, warp+32,
-    // ... of each; warps run independently (no block barrier per tile).
-    // The last warp to finish a stage refills it with the tile S ahead.
-    uint64_t c0 = 0, c1 = 0, c2 = 0;
-    bool any_bad = false;
-    const uint32_t w = p.w;
+    // Every warp walks all of the CTA's tiles, taking words warp and
+    // warp + 32 of each; warps run independently (no block barrier per
+    // tile).  The last warp to finish a stage refills it with the tile S
+    // ahead.
+    Acc acc;
     uint32_t s = 0, par = 0;
     uint64_t r0 = t0 * kTileRec;
     for (uint32_t j = 0; j < ntl; ++j) {
@@ -189,56 +284,19 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
             break;
         }
         const uint32_t cnt = (uint32_t)min((uint64_t)kTileRec, p.n_rec - r0);
-        const uint32_t nw = (cnt + 31) >> 5;
         const uint64_t *tile = ring + (size_t)s * kTileRec;
-        for (uint32_t wi = warp; wi < nw; wi += nwarps) {
-            const uint32_t rl = wi * 32 + lane;
-            const bool valid = rl < cnt;
-            const uint64_t rec = valid ? tile[rl] : 0ull;
-            const uint64_t a = rec & PHOS_REC_ADDR_MASK;
-            const bool st = (rec >> 63) != 0;
-            const bool bad = valid && (rec & kRsvdMask) != 0;
-            const bool cand = valid && !bad;
-            const uint32_t lm = __ballot_sync(0xffffffffu, cand);
-            bool hit = false;
-            int bi = -1;
-            if (lm) {
-                const uint32_t ld = (lm & 1u) ? 0u : (uint32_t)(__ffs(lm) - 1);
-                const uint64_t x = __shfl_sync(0xffffffffu, a, ld);
-                const int i0 = coop_search(x, base, f1, f2, n, lane);
-                if (i0 >= 0) {
-                    const uint64_t b0 = base[i0], s0 = size[i0];
-                    hit = cand && s0 >= w && (a - b0) <= s0 - w;
-                    bi = i0;
-                }
-                const bool miss = cand && !hit;
-                if (__ballot_sync(0xffffffffu, miss)) {
-                    if (miss) {
-                        const int ii = lane_search(a, base, n);
-                        if (ii >= 0 && inside(a, base[ii], size[ii], w)) {
-                            hit = true;
-                            bi = ii;
-                        }
-                    }
-                }
-            }
-            const uint8_t pm = hit ? perm[bi] : 0;
-            const bool viol = valid && (!hit || !(pm & (st ? 2 : 1)));
-            const uint32_t vw = __ballot_sync(0xffffffffu, viol);
-            if (lane == 0) p.bitmap[(r0 >> 5) + wi] = vw;
-            if (vw) {
-                const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
-                const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
-                if (lane == 0) {
-                    c0 += __popc(vw);
-                    c1 += __popc(sw);
-                    c2 += __popc(uw);
-                }
-                if (viol && hit) {
-                    atomicOr(&sv[bi >> 5], 1u << (bi & 31));
-                    if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
-                }
-                any_bad |= bad;
+        uint32_t *bmw = p.bitmap + (r0 >> 5);
+        if (cnt == kTileRec) {
+            for (uint32_t wi = warp; wi < kTileRec / 32; wi += nwarps)
+                word<true, kSmemTable>(L, tile[wi * 32 + lane], true, lane, bmw + wi, sv, svs,
+                                       acc);
+        } else {
+            const uint32_t nw = (cnt + 31) >> 5;
+            for (uint32_t wi = warp; wi < nw; wi += nwarps) {
+                const uint32_t rl = wi * 32 + lane;
+                const bool valid = rl < cnt;
+                word<false, kSmemTable>(L, valid ? tile[rl] : 0ull, valid, lane, bmw + wi, sv,
+                                        svs, acc);
             }
         }
         // release the stage; the last warp out refills it
@@ -269,16 +327,15 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
         // still in flight before the CTA's shared memory is released
         if (tid == 0) {
             for (uint32_t q = 0; q < S; ++q)
-                if (issued[q] != ~0u)
-                    mbar_wait_bounded(&mbar[q], (issued[q] / S) & 1u);
+                if (issued[q] != ~0u) mbar_wait_bounded(&mbar[q], (issued[q] / S) & 1u);
             set_status(p.status, PHOS_ETIMEDOUT);
         }
     }
-    if (__any_sync(0xffffffffu, any_bad) && lane == 0) set_status(p.status, PHOS_EINVAL);
-    if (lane == 0 && (c0 | c1 | c2)) {
-        atomicAdd(&red[0], (unsigned long long)c0);
-        atomicAdd(&red[1], (unsigned long long)c1);
-        atomicAdd(&red[2], (unsigned long long)c2);
+    if (__any_sync(0xffffffffu, acc.bad) && lane == 0) set_status(p.status, PHOS_EINVAL);
+    if (lane == 0 && (acc.c0 | acc.c1 | acc.c2)) {
+        atomicAdd(&red[0], (unsigned long long)acc.c0);
+        atomicAdd(&red[1], (unsigned long long)acc.c1);
+        atomicAdd(&red[2], (unsigned long long)acc.c2);
     }
     __syncthreads();
     if (tid == 0) {
@@ -326,10 +383,221 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
     }
 }
 
+// Batched-leader variant.  A warp takes 1024 consecutive records (32
+// bitmap words) at a time.  Lane j loads the first record of word j and
+// runs its own binary search for it, so the 32 searches of a batch run in
+// parallel across the lanes; the interval found for word j (base, limit,
+// permission) is parked in the warp's shared-memory slot.  Then, word by
+// word, every lane checks its record against that interval with one
+// unsigned compare (broadcast reads), lanes that miss run their own
+// search, and the batch's 32 bitmap words leave in one coalesced store.
+// Records stream straight from HBM into registers, eight words ahead.
+constexpr uint32_t kBatch = 1024;
+
+struct Lead {
+    uint64_t b, l;     // base and limit of word j's leader interval
+    int32_t i;         // its table index, -1 if none
+    uint32_t pm;       // its permission byte
+};
+
+template <bool kSmemTable, bool kFull>
+__device__ __forceinline__ void batch_words(const Look &L, const uint64_t *recs, uint64_t nb,
+                                            uint32_t lane, const Lead *lead, uint32_t *bm,
+                                            uint32_t *sv, uint32_t *svs, Acc &acc) {
+    uint32_t myvw = 0;
+#pragma unroll 1
+    for (uint32_t j0 = 0; j0 < 32; j0 += 8) {
+        uint64_t r[8];
+#pragma unroll
+        for (uint32_t u = 0; u < 8; ++u) {
+            const uint32_t k = (j0 + u) * 32 + lane;
+            r[u] = (kFull || k < nb) ? recs[k] : 0ull;
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 8; ++u) {
+            const uint32_t j = j0 + u;
+            const bool valid = kFull || (j * 32 + lane) < nb;
+            const uint64_t rec = r[u];
+            const uint64_t a = rec & PHOS_REC_ADDR_MASK;
+            const uint32_t hi = (uint32_t)(rec >> 32);
+            const bool st = (int32_t)hi < 0;
+            const bool bad = (hi & 0x7E000000u) != 0;
+            const Lead ld = lead[j];
+            bool hit = valid && !bad && (a - ld.b) < ld.l;
+            int bi = ld.i;
+            uint32_t pm = ld.pm;
+            const bool miss = valid && !bad && !hit;
+            if (__ballot_sync(0xffffffffu, miss)) {
+                if (miss) {
+                    const int ii = L.lane_search(a);
+                    if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
+                        hit = true;
+                        bi = ii;
+                        pm = L.perm[ii];
+                    }
+                }
+            }
+            const bool viol = valid && !(hit && (pm & (st ? 2u : 1u)));
+            const uint32_t vw = __ballot_sync(0xffffffffu, viol);
+            myvw = (lane == j) ? vw : myvw;
+            if (vw) {
+                const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
+                const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
+                if (lane == 0) {
+                    acc.c0 += __popc(vw);
+                    acc.c1 += __popc(sw);
+                    acc.c2 += __popc(uw);
+                }
+                if (viol && hit) {
+                    atomicOr(&sv[bi >> 5], 1u << (bi & 31));
+                    if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
+                }
+                acc.bad |= bad;
+            }
+        }
+    }
+    if (kFull || lane * 32 < nb) bm[lane] = myvw;
+}
+
+template <bool kSmemTable>
+__global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t n = p.tab.n, nvw = p.nvw;
+    Lead *leads = reinterpret_cast<Lead *>(smem);             // [nwarps][32]
+    uint8_t *cur = smem + sizeof(Lead) * 32 * nwarps;
+    unsigned long long *red = reinterpret_cast<unsigned long long *>(cur);
+    uint32_t *last = reinterpret_cast<uint32_t *>(cur + 24);
+    cur += 32;
+    const uint32_t nf1 = (n + 31) >> 5, nf2 = (n + 1023) >> 10;
+    Look L;
+    L.n = n;
+    L.nf1 = nf1;
+    L.w = p.w;
+    L.base = p.tab.base;
+    L.size = p.tab.size;
+    L.lim = nullptr;
+    L.f1 = p.tab.fence1;
+    L.f2 = p.tab.fence2;
+    L.rf = 0;
+    if (kSmemTable) {
+        uint64_t *tb = reinterpret_cast<uint64_t *>(cur);
+        uint64_t *tl = tb + n;
+        const uint32_t w = p.w;
+        for (uint32_t i = tid; i < n; i += blockDim.x) {
+            tb[i] = __ldg(p.tab.base + i);
+            const uint64_t sz = __ldg(p.tab.size + i);
+            tl[i] = sz >= w ? sz - w + 1 : 0;
+        }
+        L.base = tb;
+        L.lim = tl;
+        cur += 16ull * n;
+    }
+    uint8_t *perm = cur;
+    cur += (n + 15) & ~15u;
+    uint32_t *sv = reinterpret_cast<uint32_t *>(cur);
+    uint32_t *svs = sv + nvw;
+    L.perm = perm;
+    for (uint32_t i = tid; i < n; i += blockDim.x) perm[i] = p.perm[i];
+    for (uint32_t i = tid; i < nvw; i += blockDim.x) sv[i] = svs[i] = 0;
+    if (tid == 0) red[0] = red[1] = red[2] = 0;
+    __syncthreads();
+
+    const uint64_t G = gridDim.x, c = blockIdx.x;
+    const uint64_t nbatch = (p.n_rec + kBatch - 1) / kBatch;
+    const uint64_t b0 = nbatch * c / G, b1 = nbatch * (c + 1) / G;
+    Lead *mine = leads + 32 * warp;
+    Acc acc;
+    for (uint64_t bt = b0 + warp; bt < b1; bt += nwarps) {
+        const uint64_t r0 = bt * kBatch;
+        const uint64_t nb = min((uint64_t)kBatch, p.n_rec - r0);
+        const uint64_t *recs = p.trace + r0;
+        // leaders: lane j searches the first record of word j
+        {
+            Lead ld;
+            ld.b = 0;
+            ld.l = 0;
+            ld.i = -1;
+            ld.pm = 0;
+            if (lane * 32 < nb) {
+                const uint64_t x = recs[lane * 32] & PHOS_REC_ADDR_MASK;
+                const int i = L.lane_search(x);
+                if (i >= 0) {
+                    ld.b = L.base[i];
+                    ld.l = L.limit(i, kSmemTable);
+                    ld.i = i;
+                    ld.pm = L.perm[i];
+                }
+            }
+            mine[lane] = ld;
+        }
+        __syncwarp();
+        uint32_t *bm = p.bitmap + (r0 >> 5);
+        if (nb == kBatch)
+            batch_words<kSmemTable, true>(L, recs, nb, lane, mine, bm, sv, svs, acc);
+        else
+            batch_words<kSmemTable, false>(L, recs, nb, lane, mine, bm, sv, svs, acc);
+        __syncwarp();
+    }
+    if (__any_sync(0xffffffffu, acc.bad) && lane == 0) set_status(p.status, PHOS_EINVAL);
+    if (lane == 0 && (acc.c0 | acc.c1 | acc.c2)) {
+        atomicAdd(&red[0], (unsigned long long)acc.c0);
+        atomicAdd(&red[1], (unsigned long long)acc.c1);
+        atomicAdd(&red[2], (unsigned long long)acc.c2);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        p.cta_cnt[c * 4 + 0] = red[0];
+        p.cta_cnt[c * 4 + 1] = red[1];
+        p.cta_cnt[c * 4 + 2] = red[2];
+    }
+    for (uint32_t i = tid; i < nvw; i += blockDim.x) {
+        if (sv[i]) atomicOr(&p.vacc[i], sv[i]);
+        if (svs[i]) atomicOr(&p.vacc[nvw + i], svs[i]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *last = (atomicAdd(p.ticket, 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
+    __syncthreads();
+    if (!*last) return;
+    __threadfence();
+    if (tid == 0) red[0] = red[1] = red[2] = 0;
+    __syncthreads();
+    unsigned long long a0 = 0, a1 = 0, a2 = 0;
+    for (uint64_t q = tid; q < G; q += blockDim.x) {
+        a0 += __ldcg(p.cta_cnt + q * 4 + 0);
+        a1 += __ldcg(p.cta_cnt + q * 4 + 1);
+        a2 += __ldcg(p.cta_cnt + q * 4 + 2);
+    }
+    if (a0 | a1 | a2) {
+        atomicAdd(&red[0], a0);
+        atomicAdd(&red[1], a1);
+        atomicAdd(&red[2], a2);
+    }
+    for (uint32_t i = tid; i < nvw; i += blockDim.x) {
+        const uint32_t v = __ldcg(p.vacc + i), vs = __ldcg(p.vacc + nvw + i);
+        if (p.victim) p.victim[i] = v;
+        if (p.victim_st) p.victim_st[i] = vs;
+        p.vacc[i] = 0;
+        p.vacc[nvw + i] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        p.count[0] = red[0];
+        p.count[1] = red[1];
+        p.count[2] = red[2];
+        *p.ticket = 0;
+    }
+}
+
 // Ascending list of the first cap violating record indices.
+// units / unit_words: the main kernel's per-CTA partition (CTA c owns
+// units [units*c/G, units*(c+1)/G), each unit_words bitmap words).
 __global__ void __launch_bounds__(512) k_validate_emit(const uint32_t *bitmap, uint64_t n_rec,
-                                                       uint64_t tiles, const uint64_t *cta_cnt,
-                                                       uint64_t *idx, uint64_t cap) {
+                                                       uint64_t units, uint32_t unit_words,
+                                                       const uint64_t *cta_cnt, uint64_t *idx,
+                                                       uint64_t cap) {
     __shared__ unsigned long long s_pre;
     __shared__ uint32_t s_warp[16];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -343,9 +611,9 @@ __global__ void __launch_bounds__(512) k_validate_emit(const uint32_t *bitmap, u
     __syncthreads();
     uint64_t prefix = s_pre;
     if (prefix >= cap) return;
-    const uint64_t t0 = tiles * c / G, t1 = tiles * (c + 1) / G;
+    const uint64_t t0 = units * c / G, t1 = units * (c + 1) / G;
     const uint64_t nwords = (n_rec + 31) / 32;
-    const uint64_t w0 = t0 * (kTileRec / 32), w1 = min(t1 * (kTileRec / 32), nwords);
+    const uint64_t w0 = t0 * unit_words, w1 = min(t1 * unit_words, nwords);
     for (uint64_t wb = w0; wb < w1; wb += blockDim.x) {
         const uint64_t wi = wb + tid;
         uint32_t v = wi < w1 ? bitmap[wi] : 0u;
@@ -398,9 +666,29 @@ static ValPlan plan_validate(uint32_t n, int device) {
     return {false, S, need};
 }
 
+static size_t plan_batched(uint32_t n, int device, bool *smem_table) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (optin <= 0) optin = 227 * 1024;
+    const uint32_t nvw = (n + 31) / 32;
+    const size_t fixed = sizeof(Lead) * 32 * (kValThreads / 32) + 32 + ((n + 15) & ~15u) +
+                         8ull * nvw;
+    const size_t tab = 16ull * n;
+    *smem_table = fixed + tab <= (size_t)optin;
+    return *smem_table ? fixed + tab : fixed;
+}
+
+static uint32_t g_val_variant = 0;  // 0 auto, 1 TMA ring, 2 batched leaders
+
 }  // namespace phos
 
 using namespace phos;
+
+extern "C" phos_status phos_validate_config(uint32_t variant) {
+    if (variant > 2) return fail(PHOS_EINVAL, "validate_config: variant %u", variant);
+    g_val_variant = variant;
+    return PHOS_OK;
+}
 
 extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
                                      const uint64_t *d_trace, uint64_t n_rec,
@@ -419,9 +707,11 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     if (idx_cap && !d_idx) return fail(PHOS_EINVAL, "validate: idx_cap > 0 with NULL d_idx");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     phos_table *T = const_cast<phos_table *>(t);
-    const uint64_t tiles = (n_rec + kTileRec - 1) / kTileRec;
+    const uint32_t variant = g_val_variant == 0 ? 2u : g_val_variant;
+    const uint64_t unit = variant == 1 ? kTileRec : kBatch;
+    const uint64_t units = (n_rec + unit - 1) / unit;
     const int sms = sm_count(T->device);
-    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms, tiles));
+    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms, units));
     const uint32_t nvw = (t->n + 31) / 32;
     const size_t off_vacc = 256, off_cnt = align_up(off_vacc + 8ull * std::max(nvw, 1u), 256);
     const size_t need = off_cnt + 32ull * (size_t)sms;
@@ -436,7 +726,7 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     p.perm = d_perm;
     p.trace = d_trace;
     p.n_rec = n_rec;
-    p.tiles = tiles;
+    p.tiles = (n_rec + kTileRec - 1) / kTileRec;
     p.bitmap = d_bitmap;
     p.count = d_count;
     p.victim = d_victim;
@@ -447,31 +737,43 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     p.cta_cnt = reinterpret_cast<uint64_t *>(sc + off_cnt);
     p.w = access_bytes;
     p.nvw = nvw;
-    ValPlan pl = plan_validate(t->n, T->device);
-    p.stages = pl.stages;
-    static bool attr_done[2] = {false, false};
-    if (pl.smem_table) {
-        if (!attr_done[0]) {
-            PHOS_CUDA(cudaFuncSetAttribute(k_validate<true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+    p.stages = 0;
+    static bool attr_done[4] = {false, false, false, false};
+    auto attr = [&](const void *fn, int slot) -> phos_status {
+        if (!attr_done[slot]) {
+            PHOS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            227 * 1024));
-            attr_done[0] = true;
+            attr_done[slot] = true;
         }
-        k_validate<true><<<(unsigned)G, kValThreads, pl.smem, s>>>(p);
-        count_launch();
+        return PHOS_OK;
+    };
+    phos_status r;
+    if (variant == 1) {
+        ValPlan pl = plan_validate(t->n, T->device);
+        p.stages = pl.stages;
+        if (pl.smem_table) {
+            if ((r = attr((const void *)k_validate<true>, 0))) return r;
+            k_validate<true><<<(unsigned)G, kValThreads, pl.smem, s>>>(p);
+        } else {
+            if ((r = attr((const void *)k_validate<false>, 1))) return r;
+            k_validate<false><<<(unsigned)G, kValThreads, pl.smem, s>>>(p);
+        }
     } else {
-        if (!attr_done[1]) {
-            PHOS_CUDA(cudaFuncSetAttribute(k_validate<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           227 * 1024));
-            attr_done[1] = true;
+        bool smem_table;
+        const size_t smem = plan_batched(t->n, T->device, &smem_table);
+        if (smem_table) {
+            if ((r = attr((const void *)k_validate_b<true>, 2))) return r;
+            k_validate_b<true><<<(unsigned)G, kValThreads, smem, s>>>(p);
+        } else {
+            if ((r = attr((const void *)k_validate_b<false>, 3))) return r;
+            k_validate_b<false><<<(unsigned)G, kValThreads, smem, s>>>(p);
         }
-        k_validate<false><<<(unsigned)G, kValThreads, pl.smem, s>>>(p);
-        count_launch();
     }
+    count_launch();
     PHOS_CUDA(cudaGetLastError());
     if (d_idx && idx_cap && n_rec) {
-        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, tiles, p.cta_cnt, d_idx,
+        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, units,
+                                                    (uint32_t)(unit / 32), p.cta_cnt, d_idx,
                                                     idx_cap);
         count_launch();
         PHOS_CUDA(cudaGetLastError());

@@ -1,0 +1,165 @@
+"""Kernel microbenchmarks of the data plane (CUDA events, after warm-up).
+
+    python -m paper_2405_12079_b300.kernels_bench [--kernel validate|copy|all]
+                                                  [--traces K] [--copy-gb G]
+
+validate: one launch over K concatenated 1.3M-record training-kernel traces
+          (1,000-buffer table; K = 160 -> 208M records, 1.7 GB), plus one
+          launch per single trace, plus a random-record trace.
+copy:     G GB of 4 MB regions device->device, device->pinned host and
+          pinned host->device through the copy engine, next to the DMA
+          engines (torch copy_) on the same buffers.
+Prints one JSON object.  Inputs are larger than L2 unless stated.
+"""
+import argparse
+import json
+import sys
+
+import numpy as np
+import torch
+
+from . import phos, workloads as wl
+
+VA0 = 0x7E00_0000_0000
+
+
+def timeit(fn, reps=10, warm=3):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def bench_validate(K, out, variants=(1, 2)):
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(n_kernels=1)
+    lay, rng = cfg["layout"], cfg["rng"]
+    t = phos.Table(lay.base(VA0), lay.size)
+    reads, writes = wl.pick_sets(rng, lay.n)
+    perm = np.zeros(lay.n, np.uint8)
+    perm[reads] = phos.PERM_R
+    perm[writes] = phos.PERM_RW
+    rec, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, 1_300_000, 0.001, 0.0)
+    big = torch.from_numpy(np.tile(rec, K).view(np.uint8)).cuda()
+    N = len(rec) * K
+    d_perm = torch.from_numpy(perm).cuda()
+    bm = torch.empty(((N + 31) // 32) * 4, dtype=torch.uint8, device="cuda")
+    cnt = torch.empty(24, dtype=torch.uint8, device="cuda")
+    vv = torch.empty(256, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(4, dtype=torch.uint8, device="cuda")
+
+    def run(ptr, nrec):
+        phos.validate(t, d_perm.data_ptr(), ptr, nrec, 4, bm.data_ptr(), cnt.data_ptr(),
+                      vv.data_ptr(), vv.data_ptr() + 128, None, 0, st.data_ptr(), s)
+
+    n1 = len(rec)
+    rr, _ = wl.trace_random(rng, lay, VA0, np.asarray(writes), 64 * 1_000_000)
+    rrd = torch.from_numpy(rr.view(np.uint8)).cuda()
+    for v in variants:
+        phos.validate_config(v)
+        tag = "v%d" % v
+        ms = timeit(lambda: run(big.data_ptr(), N))
+        out["validate_concat_" + tag] = dict(records=N, ms=ms, grec_s=N / ms / 1e6,
+                                             gbs=N * 8.125 / ms / 1e6)
+        ms = timeit(lambda: [run(big.data_ptr() + 8 * n1 * j, n1) for j in range(K)], 3, 1) / K
+        out["validate_per_trace_" + tag] = dict(records=n1, us=1e3 * ms, grec_s=n1 / ms / 1e6,
+                                                gbs=n1 * 8.125 / ms / 1e6)
+        ms = timeit(lambda: run(rrd.data_ptr(), len(rr)))
+        out["validate_random_" + tag] = dict(records=len(rr), ms=ms, grec_s=len(rr) / ms / 1e6)
+    phos.validate_config(0)
+
+
+def bench_copy(gb, out):
+    s = torch.cuda.current_stream().cuda_stream
+    G = int(gb) << 30
+    live = torch.empty(G, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(live.data_ptr(), G, 5, s)
+    nb = 64
+    bs = G // nb
+    tab = phos.Table([live.data_ptr() + i * bs for i in range(nb)], [bs] * nb)
+    stg = torch.empty(G, dtype=torch.uint8, device="cuda")
+    img = torch.empty(G, dtype=torch.uint8).pin_memory()
+    st = torch.zeros(4, dtype=torch.uint8, device="cuda")
+
+    def mk(kind, chunk=4 << 20):
+        rows = []
+        for i in range(nb):
+            for o in range(0, bs, chunk):
+                rows.append((o, i * bs + o, chunk, i, kind) if kind != 4 else
+                            (i * bs + o, o, chunk, i, kind))
+        a = np.array(rows, phos.COPY_DTYPE)
+        return torch.from_numpy(a.view(np.uint8)).cuda(), len(rows)
+
+    d1, n1 = mk(phos.COPY_LIVE_TO_STAGING)
+    d2, n2 = mk(phos.COPY_LIVE_TO_IMAGE)
+    d4, n4 = mk(phos.COPY_IMAGE_TO_LIVE)
+    ms = timeit(lambda: phos.cow_copy(tab, d1.data_ptr(), n1, stg.data_ptr(), G, st.data_ptr(), s),
+                5, 2)
+    out["copy_d2d"] = dict(gb=gb, ms=ms, gbs_rw=2 * G / ms / 1e6)
+    ms = timeit(lambda: phos.recopy(tab, d2.data_ptr(), n2, img.data_ptr(), G, st.data_ptr(), s),
+                3, 1)
+    out["copy_d2h"] = dict(gb=gb, ms=ms, gbs=G / ms / 1e6)
+    ms = timeit(lambda: phos.restore_on_demand(tab, d4.data_ptr(), n4, img.data_ptr(), G, None,
+                                               st.data_ptr(), s), 3, 1)
+    out["copy_h2d"] = dict(gb=gb, ms=ms, gbs=G / ms / 1e6)
+    ms = timeit(lambda: stg.copy_(live, non_blocking=True), 5, 2)
+    out["dma_d2d"] = dict(gbs_rw=2 * G / ms / 1e6)
+    ms = timeit(lambda: img.copy_(live, non_blocking=True), 3, 1)
+    out["dma_d2h"] = dict(gbs=G / ms / 1e6)
+    ms = timeit(lambda: live.copy_(img, non_blocking=True), 3, 1)
+    out["dma_h2d"] = dict(gbs=G / ms / 1e6)
+    # two DMA streams, and DMA + copy engine at once, device -> host
+    h2 = torch.empty(G // 2, dtype=torch.uint8).pin_memory()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    half = G // 2
+    cur = torch.cuda.current_stream()
+
+    def two_dma():
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            img[:half].copy_(live[:half], non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(live[half:], non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+    ms = timeit(two_dma, 3, 1)
+    out["dma_d2h_two_streams"] = dict(gbs=G / ms / 1e6)
+
+    def dma_and_engine():
+        s1.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            h2.copy_(live[half:], non_blocking=True)
+        phos.recopy(tab, d2.data_ptr(), n2 // 2, img.data_ptr(), G, st.data_ptr(), s)
+        cur.wait_stream(s1)
+    ms = timeit(dma_and_engine, 3, 1)
+    out["dma_and_engine_d2h"] = dict(gbs=G / ms / 1e6)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kernel", default="all", choices=["validate", "copy", "all"])
+    ap.add_argument("--traces", type=int, default=160)
+    ap.add_argument("--copy-gb", type=int, default=8)
+    ap.add_argument("--variant", type=int, default=0, help="validate kernel variant (0 = both)")
+    a = ap.parse_args()
+    out = {}
+    if a.kernel in ("validate", "all"):
+        bench_validate(a.traces, out, (1, 2) if a.variant == 0 else (a.variant,))
+    if a.kernel in ("copy", "all"):
+        bench_copy(a.copy_gb, out)
+    print(json.dumps(out, indent=1))
+    sys.stdout.flush()
+
+
+if __name__ == "__main__":
+    main()

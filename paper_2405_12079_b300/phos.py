@@ -47,6 +47,7 @@ _SIGS = {
     "phos_restore_on_demand": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _vp, _vp]),
     "phos_copy": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
     "phos_copy_config": (_i32, [_u64, _u32]),
+    "phos_validate_config": (_i32, [_u32]),
     "phos_image_bytes": (_u64, [_vp]),
     "phos_image_offsets": (_i32, [_vp, _vp]),
     "phos_harness_digest": (_i32, [_vp, _vp, _u32, _vp, _vp]),
@@ -223,6 +224,10 @@ def copy(table, d_list, n, d_staging=None, staging_bytes=0, image=None, image_by
          d_present=None, d_status=None, stream=None):
     return check(lib().phos_copy(table.handle, d_list, n, d_staging, staging_bytes, image,
                                  image_bytes, d_present, d_status, stream), "copy")
+
+
+def validate_config(variant=0):
+    return check(lib().phos_validate_config(variant), "validate_config")
 
 
 def copy_config(tile_bytes=0, ctas_per_sm=0):

@@ -22,6 +22,14 @@ from gpu_util import run_validate  # noqa: E402
 VA0 = 0x7E00_0000_0000
 
 
+@pytest.fixture(autouse=True, params=[1, 2], ids=["ring", "batched"])
+def variant(request):
+    """Every case runs on both kernel variants."""
+    phos.validate_config(request.param)
+    yield request.param
+    phos.validate_config(0)
+
+
 def check(table, base, size, perm, trace, w, idx_cap=0):
     got = run_validate(table, perm, trace, w, idx_cap)
     exp = core.validate(base, size, perm, trace, w, idx_cap)
