@@ -160,6 +160,32 @@ phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
                           uint32_t *d_victim_st, uint64_t *d_idx, uint64_t idx_cap,
                           uint32_t *d_status, phos_stream_t stream);
 
+/* phos_validate for callers that cannot allocate device memory.  The paper
+ * has no counterpart: it exists for this library's users.  Examples are an
+ * interposer validating from inside an application's intercepted CUDA call
+ * (allocating there can re-enter the interception layer or deadlock on the
+ * application's allocator lock) and callers that must not let cudaMalloc's
+ * implicit device synchronisation stall the application's kernels during a
+ * concurrent checkpoint.
+ * Same arguments, results and error behaviour as phos_validate, but the
+ * call allocates nothing: its scratch (per-CTA counts, victim accumulators,
+ * a completion ticket; 12.5 KB) is a fixed array inside the library that
+ * every GPU which loads the library holds until the process exits.
+ * Limits: tables of at most 16384 buffers (larger ones get PHOS_EINVAL and
+ * a message; use phos_validate for them) and at most 256 CTAs per launch
+ * (the call never launches more).  The first call on a device looks the array up on
+ * that device (it makes the device current for the lookup and restores
+ * the previous one); make that first call before any stream capture.
+ * Every call clears the parts of the array it uses, then launches; all
+ * calls share the one array, so calls that overlap on the GPU (concurrent
+ * streams, or several host threads) race and must be ordered by the
+ * caller. */
+phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_t *d_perm,
+                                  const uint64_t *d_trace, uint64_t n_rec,
+                                  uint32_t access_bytes, uint32_t *d_bitmap, uint64_t *d_count,
+                                  uint32_t *d_victim, uint32_t *d_victim_st, uint64_t *d_idx,
+                                  uint64_t idx_cap, uint32_t *d_status, phos_stream_t stream);
+
 /* Kernel variant of phos_validate (process-wide; the autotuner sets it):
  * 0 = default, 1 = bulk-copy ring with one warp-cooperative search per
  * 32 records, 2 = batched leaders (each lane searches the first record of

@@ -780,3 +780,133 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     }
     return PHOS_OK;
 }
+
+// ----------------------------------------------------------------------
+// phos_validate_noalloc: phos_validate without any device allocation.
+//
+// Some callers cannot call cudaMalloc when they validate: the interposer
+// that runs inside an application's intercepted CUDA call (where entering
+// the allocator again can deadlock on the application's allocator lock or
+// recurse into the interception layer), and callers that must not let an
+// allocation's implicit device synchronisation stall the application's
+// in-flight kernels during a concurrent checkpoint.  This entry point
+// keeps its scratch (per-CTA counts, victim accumulators, completion
+// ticket) in a fixed array inside the library instead of the table
+// handle's growable scratch.
+// ----------------------------------------------------------------------
+namespace phos {
+
+constexpr uint32_t kNoallocMaxCtas = 256;
+constexpr uint32_t kNoallocMaxBuffers = 16384;
+constexpr size_t kNoallocOffVacc = 256;
+constexpr size_t kNoallocOffCnt = kNoallocOffVacc + 8ull * ((kNoallocMaxBuffers + 31) / 32);
+constexpr size_t kNoallocBytes = kNoallocOffCnt + 32ull * kNoallocMaxCtas;
+
+// Every GPU that loads the library holds this array until the process
+// exits.  All calls share it.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[64];
+
+// Zero the ticket and the victim accumulators this call will use.
+__global__ void k_noalloc_clear(uint8_t *scratch, uint32_t nvw) {
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(scratch);
+    uint32_t *vacc = reinterpret_cast<uint32_t *>(scratch + kNoallocOffVacc);
+    if (threadIdx.x == 0) *ticket = 0;
+    for (uint32_t i = threadIdx.x; i < 2 * nvw; i += blockDim.x) vacc[i] = 0;
+}
+
+// Device address of the array on the table's device, looked up once per
+// device with that device current.
+static phos_status noalloc_scratch(int device, void **out) {
+    if (device < 0 || device >= 64) return fail(PHOS_EINVAL, "validate_noalloc: device %d", device);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        int cur = -1;
+        PHOS_CUDA(cudaGetDevice(&cur));
+        if (cur != device) PHOS_CUDA(cudaSetDevice(device));
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (cur != device) cudaSetDevice(cur);
+        if (e != cudaSuccess) return cuda_fail(e, "validate_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return PHOS_OK;
+}
+
+}  // namespace phos
+
+extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_t *d_perm,
+                                             const uint64_t *d_trace, uint64_t n_rec,
+                                             uint32_t access_bytes, uint32_t *d_bitmap,
+                                             uint64_t *d_count, uint32_t *d_victim,
+                                             uint32_t *d_victim_st, uint64_t *d_idx,
+                                             uint64_t idx_cap, uint32_t *d_status,
+                                             phos_stream_t stream) {
+    if (!t) return fail(PHOS_EINVAL, "validate_noalloc: table is NULL");
+    if (!d_count) return fail(PHOS_EINVAL, "validate_noalloc: d_count is NULL");
+    if (access_bytes == 0) return fail(PHOS_EINVAL, "validate_noalloc: access_bytes is 0");
+    if (n_rec && (!d_trace || !d_bitmap))
+        return fail(PHOS_EINVAL, "validate_noalloc: NULL trace or bitmap");
+    if (n_rec && ((uintptr_t)d_trace & 15))
+        return fail(PHOS_EINVAL, "validate_noalloc: trace must be 16-byte aligned");
+    if (t->n && !d_perm) return fail(PHOS_EINVAL, "validate_noalloc: d_perm is NULL");
+    if (idx_cap && !d_idx) return fail(PHOS_EINVAL, "validate_noalloc: idx_cap > 0 with NULL d_idx");
+    if (t->n > kNoallocMaxBuffers)
+        return fail(PHOS_EINVAL,
+                    "validate_noalloc: table of %u buffers exceeds the fixed scratch limit of %u "
+                    "buffers; use phos_validate",
+                    t->n, kNoallocMaxBuffers);
+    void *scr = nullptr;
+    phos_status r = noalloc_scratch(t->device, &scr);
+    if (r) return r;
+    uint8_t *sc = static_cast<uint8_t *>(scr);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint64_t units = (n_rec + kBatch - 1) / kBatch;
+    const uint64_t G = std::max<uint64_t>(
+        1, std::min<uint64_t>(std::min<uint64_t>((uint64_t)sm_count(t->device), kNoallocMaxCtas),
+                              units));
+    const uint32_t nvw = (t->n + 31) / 32;
+    ValParams p;
+    p.tab = t->view;
+    p.perm = d_perm;
+    p.trace = d_trace;
+    p.n_rec = n_rec;
+    p.tiles = (n_rec + kTileRec - 1) / kTileRec;
+    p.bitmap = d_bitmap;
+    p.count = d_count;
+    p.victim = d_victim;
+    p.victim_st = d_victim_st;
+    p.status = d_status;
+    p.ticket = reinterpret_cast<uint32_t *>(sc);
+    p.vacc = reinterpret_cast<uint32_t *>(sc + kNoallocOffVacc);
+    p.cta_cnt = reinterpret_cast<uint64_t *>(sc + kNoallocOffCnt);
+    p.w = access_bytes;
+    p.nvw = nvw;
+    p.stages = 0;
+    k_noalloc_clear<<<1, 256, 0, s>>>(sc, nvw);
+    count_launch();
+    PHOS_CUDA(cudaGetLastError());
+    bool smem_table;
+    const size_t smem = plan_batched(t->n, t->device, &smem_table);
+    if (smem_table) {
+        PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_b<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        k_validate_b<true><<<(unsigned)G, kValThreads, smem, s>>>(p);
+    } else {
+        PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_b<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        k_validate_b<false><<<(unsigned)G, kValThreads, smem, s>>>(p);
+    }
+    count_launch();
+    PHOS_CUDA(cudaGetLastError());
+    if (d_idx && idx_cap && n_rec) {
+        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, units, kBatch / 32,
+                                                    p.cta_cnt, d_idx, idx_cap);
+        count_launch();
+        PHOS_CUDA(cudaGetLastError());
+    }
+    return PHOS_OK;
+}

@@ -48,6 +48,8 @@ _SIGS = {
     "phos_copy": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
     "phos_copy_config": (_i32, [_u64, _u32]),
     "phos_validate_config": (_i32, [_u32]),
+    "phos_validate_noalloc": (_i32, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _u64,
+                                      _vp, _vp]),
     "phos_image_bytes": (_u64, [_vp]),
     "phos_image_offsets": (_i32, [_vp, _vp]),
     "phos_harness_digest": (_i32, [_vp, _vp, _u32, _vp, _vp]),
@@ -202,6 +204,15 @@ def validate(table, d_perm, d_trace, n_rec, access_bytes, d_bitmap, d_count, d_v
     return check(lib().phos_validate(table.handle, d_perm, d_trace, n_rec, access_bytes,
                                      d_bitmap, d_count, d_victim, d_victim_st, d_idx, idx_cap,
                                      d_status, stream), "validate")
+
+
+def validate_noalloc(table, d_perm, d_trace, n_rec, access_bytes, d_bitmap, d_count,
+                     d_victim=None, d_victim_st=None, d_idx=None, idx_cap=0, d_status=None,
+                     stream=None):
+    """phos_validate_noalloc: the same validation, no device allocation."""
+    return check(lib().phos_validate_noalloc(table.handle, d_perm, d_trace, n_rec, access_bytes,
+                                             d_bitmap, d_count, d_victim, d_victim_st, d_idx,
+                                             idx_cap, d_status, stream), "validate_noalloc")
 
 
 def cow_copy(table, d_list, n, d_staging, staging_bytes, d_status=None, stream=None):
