@@ -235,6 +235,121 @@ phos_status phos_copy_config(uint64_t tile_bytes, uint32_t ctas_per_sm);
 uint64_t phos_image_bytes(const phos_table_t *t);
 phos_status phos_image_offsets(const phos_table_t *t, uint64_t *img_off_out);
 
+/* ---------------------------------------------------------- batched plan
+ *
+ * Many process images' validation traces and copy lists in one persistent
+ * launch, replayed as a CUDA graph.  Per item, the results are exactly those
+ * of phos_validate (no index list) and phos_copy on the same arguments.
+ * Items are independent images: no item's copies may write what another
+ * item reads or writes.  Present marks (restore) are not supported here. */
+
+typedef struct phos_plan phos_plan_t;
+
+typedef struct {
+    const phos_table_t *table;   /* the item's buffer table                  */
+    const uint8_t *d_perm;       /* device u8[n], speculated permissions      */
+    const uint64_t *d_trace;     /* device, 16-byte aligned; n_rec records    */
+    uint64_t n_rec;
+    uint32_t access_bytes;       /* >= 1 when n_rec > 0                       */
+    uint32_t n_copy;             /* descriptors in d_list                     */
+    uint32_t *d_bitmap;          /* outputs as in phos_validate; d_count is   */
+    uint64_t *d_count;           /* required, the victim bitmaps may be NULL  */
+    uint32_t *d_victim;
+    uint32_t *d_victim_st;
+    const phos_copy_t *d_list;   /* device descriptors, read once at create   */
+    void *staging;               /* the item's staging area and image         */
+    uint64_t staging_bytes;
+    void *image;
+    uint64_t image_bytes;
+} phos_plan_item_t;
+
+/* Resolve and check every descriptor (host side, once; synchronous), size
+ * the plan's shared memory for its largest table (EINVAL if it does not
+ * fit) and capture the launch as a CUDA graph.  The plan keeps the item
+ * pointers: the caller keeps that memory alive and unchanged in place
+ * (contents may change between launches: traces, permissions and the
+ * bytes being copied are read at launch time). */
+phos_status phos_plan_create(const phos_plan_item_t *items, uint32_t n_items,
+                             phos_plan_t **out);
+/* One graph launch on the stream: validation of every item, then every
+ * copy; outputs overwritten. */
+phos_status phos_plan_launch(phos_plan_t *p, phos_stream_t stream);
+/* Copy work-item size (multiple of 4 KiB, 4 KiB .. 16 MiB); re-captures. */
+phos_status phos_plan_set_tile(phos_plan_t *p, uint64_t tile_bytes);
+/* Autotuner: times the plan at tile sizes 64 KiB .. 4 MiB (two warm-up and
+ * five timed launches each, best of five) and keeps the fastest.  The
+ * launches really run: outputs and copies are produced each time. */
+phos_status phos_plan_autotune(phos_plan_t *p, phos_stream_t stream, uint64_t *best_tile,
+                               float *best_ms);
+/* Totals of the plan and its device status word (synchronous copy). */
+phos_status phos_plan_info(const phos_plan_t *p, uint64_t *records, uint64_t *copy_bytes,
+                           uint64_t *tile_bytes, uint32_t *status_out);
+phos_status phos_plan_destroy(phos_plan_t *p);
+
+/* ------------------------------------------------------------ serving
+ *
+ * Continuous batching of checkpoint and restore requests (Sec. 7: periodic
+ * checkpoints for fault tolerance, restore-mostly serverless startups).  A
+ * scheduler thread admits requests as slots and the staging budget free up
+ * (a checkpoint needs staging for its whole image, a restore none, so a
+ * restore may pass a checkpoint that waits), snapshots checkpoints into
+ * staging at HBM speed, and moves every admitted request's host leg in
+ * pieces, round-robin across requests, device->host and host->device at
+ * the same time.  Pieces of >= dma_min bytes go to the DMA engines, smaller
+ * ones to the SM copy kernel.  Requests must be independent: no two
+ * requests in flight may share a table handle or overlapping memory. */
+
+typedef struct phos_server phos_server_t;
+enum { PHOS_REQ_CHECKPOINT = 1, PHOS_REQ_RESTORE = 2 };
+
+typedef struct {
+    uint32_t max_slots;      /* requests on the device at once (1 = one at a
+                                time, strictly in arrival order)            */
+    uint32_t reserved;
+    void *d_staging;         /* device staging area (checkpoint snapshots)  */
+    uint64_t staging_bytes;  /* admission budget                            */
+    uint64_t chunk;          /* host-leg piece size, multiple of 256        */
+    uint64_t dma_min;        /* pieces >= this go to the DMA engines; 0 = none */
+} phos_server_desc_t;
+
+typedef struct {
+    uint32_t kind;                /* PHOS_REQ_*                              */
+    uint32_t reserved;
+    const phos_table_t *table;    /* the process image (live device buffers) */
+    void *host;                   /* pinned image: destination of a checkpoint,
+                                     source of a restore (phos_image_offsets
+                                     layout), >= phos_image_bytes(table)     */
+    uint64_t host_bytes;
+} phos_request_t;
+
+typedef struct {
+    uint32_t state;               /* 0 queued, 1 admitted, 2 done, 3 failed  */
+    phos_status status;
+    uint64_t bytes;               /* image bytes moved                       */
+    uint64_t t_submit_ns;         /* CLOCK_MONOTONIC                         */
+    uint64_t t_admit_ns;
+    uint64_t t_done_ns;           /* the last byte is at its destination     */
+} phos_result_t;
+
+phos_status phos_server_start(const phos_server_desc_t *d, phos_server_t **out);
+/* Thread-safe; returns a ticket.  EBUDGET if the image can never fit the
+ * staging budget. */
+phos_status phos_server_submit(phos_server_t *s, const phos_request_t *r, uint64_t *ticket);
+/* Non-blocking. */
+phos_status phos_server_poll(phos_server_t *s, uint64_t ticket, phos_result_t *out);
+/* Wait until nothing is queued or in flight (ETIMEDOUT after timeout_ms). */
+phos_status phos_server_drain(phos_server_t *s, uint32_t timeout_ms);
+/* Finish what was submitted, then stop the scheduler and free its streams. */
+phos_status phos_server_stop(phos_server_t *s);
+
+/* Host legs of the protocol drivers below: pieces that cross PCIe (to or
+ * from the image) and are at least dma_min_bytes long go to the DMA copy
+ * engines (cudaMemcpyAsync, one call per piece, as the paper's prototype
+ * copies, Sec. 5) instead of the SM copy kernel; 0 keeps every piece on
+ * the SM copy kernel.  Default 1 MiB (the engines move 57 GB/s of payload
+ * over this link, SM stores 53 GB/s).  Process-wide. */
+phos_status phos_host_copy_config(uint64_t dma_min_bytes);
+
 /* ------------------------------------------------- protocol control plane
  *
  * Lockstep drivers of the three concurrent protocols.  The caller plays

@@ -17,6 +17,13 @@ namespace phos {
 
 enum : uint8_t { kPending = 0, kInflight = 1, kDone = 2 };
 
+// Host-leg pieces of at least this many bytes go to the DMA engines
+// (cudaMemcpyAsync) instead of the SM copy kernel; 0 = never.  SM-issued
+// stores reach the host in small PCIe write packets (measured 12 % link
+// overhead, 52.8 GB/s of payload) while the copy engines deliver 57.3 GB/s
+// on the same link, so large pieces default to the engines.
+static uint64_t g_dma_min = 1ull << 20;
+
 // First fit over free extents sorted by offset, coalesced on release.
 struct FirstFit {
     std::vector<std::pair<uint64_t, uint64_t>> free;  // (off, len)
@@ -127,10 +134,52 @@ struct Session {
         return PHOS_OK;
     }
 
-    // Launch one batch through the copy engine.
-    phos_status submit(const std::vector<phos_copy_t> &v, void *staging, uint64_t staging_bytes,
+    // Launch one batch through the copy engine.  With DMA enabled, host-leg
+    // pieces of at least g_dma_min bytes become cudaMemcpyAsync calls issued
+    // first; their present marks ride in the kernel batch that follows on
+    // the same stream (a zero-length descriptor), so no bit precedes its
+    // bytes.
+    phos_status submit(const std::vector<phos_copy_t> &v0, void *staging, uint64_t staging_bytes,
                        const void *image, uint64_t image_bytes, uint32_t *present) {
-        if (v.empty()) return PHOS_OK;
+        if (v0.empty()) return PHOS_OK;
+        std::vector<phos_copy_t> keep;
+        const std::vector<phos_copy_t> *vp = &v0;
+        if (g_dma_min) {
+            keep.reserve(v0.size());
+            for (const phos_copy_t &d : v0) {
+                const uint32_t dir = d.flags & PHOS_COPY_DIR_MASK;
+                const bool host_leg = dir == PHOS_COPY_LIVE_TO_IMAGE ||
+                                      dir == PHOS_COPY_STAGING_TO_IMAGE ||
+                                      dir == PHOS_COPY_IMAGE_TO_LIVE;
+                if (!host_leg || d.len < g_dma_min) {
+                    keep.push_back(d);
+                    continue;
+                }
+                const uint8_t *src;
+                uint8_t *dst;
+                if (dir == PHOS_COPY_LIVE_TO_IMAGE) {
+                    src = reinterpret_cast<const uint8_t *>(t->base[d.buf] + d.src_off);
+                    dst = static_cast<uint8_t *>(const_cast<void *>(image)) + d.dst_off;
+                } else if (dir == PHOS_COPY_STAGING_TO_IMAGE) {
+                    src = static_cast<const uint8_t *>(staging) + d.src_off;
+                    dst = static_cast<uint8_t *>(const_cast<void *>(image)) + d.dst_off;
+                } else {
+                    src = static_cast<const uint8_t *>(image) + d.src_off;
+                    dst = reinterpret_cast<uint8_t *>(t->base[d.buf] + d.dst_off);
+                }
+                PHOS_CUDA(cudaMemcpyAsync(dst, src, d.len, cudaMemcpyDefault, s));
+                if (d.flags & PHOS_COPY_MARK_PRESENT) {
+                    phos_copy_t m = d;
+                    m.len = 0;
+                    m.src_off = dir == PHOS_COPY_IMAGE_TO_LIVE ? d.src_off : 0;
+                    m.dst_off = dir == PHOS_COPY_IMAGE_TO_LIVE ? d.dst_off : 0;
+                    keep.push_back(m);
+                }
+            }
+            vp = &keep;
+            if (keep.empty()) return PHOS_OK;
+        }
+        const std::vector<phos_copy_t> &v = *vp;
         if (h_used + v.size() > h_cap) {
             PHOS_CUDA(cudaStreamSynchronize(s));
             h_used = 0;
@@ -233,6 +282,11 @@ phos_status copy_log(const std::vector<uint64_t> &log, uint64_t *out, uint64_t c
 }  // namespace phos
 
 using namespace phos;
+
+extern "C" phos_status phos_host_copy_config(uint64_t dma_min_bytes) {
+    g_dma_min = dma_min_bytes;
+    return PHOS_OK;
+}
 
 struct phos_ckpt {
     Session ss;

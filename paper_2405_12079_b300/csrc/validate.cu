@@ -33,6 +33,7 @@
 
 #include "internal.h"
 #include "ptx.cuh"
+#include "validate_dev.cuh"
 
 namespace phos {
 
@@ -60,65 +61,6 @@ struct ValParams {
     uint32_t w;
     uint32_t nvw;
     uint32_t stages;
-};
-
-// Table view used by the lookup.  lim[i] = number of valid start offsets
-// of a w-byte access in buffer i (size - w + 1, or 0 if size < w), so that
-// [a, a+w) lies in buffer i  <=>  a - base[i] < lim[i]  (unsigned; a below
-// base wraps to a huge value).
-struct Look {
-    const uint64_t *base;
-    const uint64_t *lim;     // shared-memory path
-    const uint64_t *size;    // global path: lim computed on the fly
-    const uint64_t *f1;
-    const uint64_t *f2;
-    const uint8_t *perm;
-    uint32_t n, nf1, w;
-    uint64_t rf;             // this lane's entry of the top search level
-
-    __device__ __forceinline__ uint64_t limit(int i, bool smem_lim) const {
-        if (smem_lim) return lim[i];
-        const uint64_t s = size[i];
-        return s >= w ? s - w + 1 : 0;
-    }
-
-    // Warp-uniform x: index of the last buffer with base <= x, or -1.
-    // One ballot per level; the top level lives in registers.
-    __device__ __forceinline__ int search(uint64_t x, uint32_t lane) const {
-        const uint64_t kMax = ~0ull;
-        uint32_t c = __popc(__ballot_sync(0xffffffffu, rf <= x));
-        if (n <= 32) return (int)c - 1;
-        if (c == 0) return -1;
-        uint32_t blk = c - 1;
-        if (n > 1024) {
-            const uint32_t idx = blk * 32 + lane;
-            const uint64_t v = idx < nf1 ? f1[idx] : kMax;
-            blk = blk * 32 + __popc(__ballot_sync(0xffffffffu, v <= x)) - 1;
-        }
-        const uint32_t idx = blk * 32 + lane;
-        const uint64_t v = idx < n ? base[idx] : kMax;
-        return (int)(blk * 32 + __popc(__ballot_sync(0xffffffffu, v <= x)) - 1);
-    }
-
-    // Per-lane binary search (divergent fallback).
-    __device__ __forceinline__ int lane_search(uint64_t a) const {
-        uint32_t lo = 0, cnt = n;
-        while (cnt > 0) {
-            const uint32_t half = cnt >> 1;
-            if (base[lo + half] <= a) {
-                lo += half + 1;
-                cnt -= half + 1;
-            } else {
-                cnt = half;
-            }
-        }
-        return (int)lo - 1;
-    }
-};
-
-struct Acc {
-    uint64_t c0 = 0, c1 = 0, c2 = 0;
-    bool bad = false;
 };
 
 // Classify the 32 records of one bitmap word (one per lane) and write the
@@ -381,82 +323,6 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
         p.count[2] = red[2];
         *p.ticket = 0;
     }
-}
-
-// Batched-leader variant.  A warp takes 1024 consecutive records (32
-// bitmap words) at a time.  Lane j loads the first record of word j and
-// runs its own binary search for it, so the 32 searches of a batch run in
-// parallel across the lanes; the interval found for word j (base, limit,
-// permission) is parked in the warp's shared-memory slot.  Then, word by
-// word, every lane checks its record against that interval with one
-// unsigned compare (broadcast reads), lanes that miss run their own
-// search, and the batch's 32 bitmap words leave in one coalesced store.
-// Records stream straight from HBM into registers, eight words ahead.
-constexpr uint32_t kBatch = 1024;
-
-struct Lead {
-    uint64_t b, l;     // base and limit of word j's leader interval
-    int32_t i;         // its table index, -1 if none
-    uint32_t pm;       // its permission byte
-};
-
-template <bool kSmemTable, bool kFull>
-__device__ __forceinline__ void batch_words(const Look &L, const uint64_t *recs, uint64_t nb,
-                                            uint32_t lane, const Lead *lead, uint32_t *bm,
-                                            uint32_t *sv, uint32_t *svs, Acc &acc) {
-    uint32_t myvw = 0;
-#pragma unroll 1
-    for (uint32_t j0 = 0; j0 < 32; j0 += 8) {
-        uint64_t r[8];
-#pragma unroll
-        for (uint32_t u = 0; u < 8; ++u) {
-            const uint32_t k = (j0 + u) * 32 + lane;
-            r[u] = (kFull || k < nb) ? recs[k] : 0ull;
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < 8; ++u) {
-            const uint32_t j = j0 + u;
-            const bool valid = kFull || (j * 32 + lane) < nb;
-            const uint64_t rec = r[u];
-            const uint64_t a = rec & PHOS_REC_ADDR_MASK;
-            const uint32_t hi = (uint32_t)(rec >> 32);
-            const bool st = (int32_t)hi < 0;
-            const bool bad = (hi & 0x7E000000u) != 0;
-            const Lead ld = lead[j];
-            bool hit = valid && !bad && (a - ld.b) < ld.l;
-            int bi = ld.i;
-            uint32_t pm = ld.pm;
-            const bool miss = valid && !bad && !hit;
-            if (__ballot_sync(0xffffffffu, miss)) {
-                if (miss) {
-                    const int ii = L.lane_search(a);
-                    if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
-                        hit = true;
-                        bi = ii;
-                        pm = L.perm[ii];
-                    }
-                }
-            }
-            const bool viol = valid && !(hit && (pm & (st ? 2u : 1u)));
-            const uint32_t vw = __ballot_sync(0xffffffffu, viol);
-            myvw = (lane == j) ? vw : myvw;
-            if (vw) {
-                const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
-                const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
-                if (lane == 0) {
-                    acc.c0 += __popc(vw);
-                    acc.c1 += __popc(sw);
-                    acc.c2 += __popc(uw);
-                }
-                if (viol && hit) {
-                    atomicOr(&sv[bi >> 5], 1u << (bi & 31));
-                    if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
-                }
-                acc.bad |= bad;
-            }
-        }
-    }
-    if (kFull || lane * 32 < nb) bm[lane] = myvw;
 }
 
 template <bool kSmemTable>

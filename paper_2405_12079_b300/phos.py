@@ -48,6 +48,7 @@ _SIGS = {
     "phos_copy": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
     "phos_copy_config": (_i32, [_u64, _u32]),
     "phos_validate_config": (_i32, [_u32]),
+    "phos_host_copy_config": (_i32, [_u64]),
     "phos_validate_noalloc": (_i32, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _u64,
                                       _vp, _vp]),
     "phos_image_bytes": (_u64, [_vp]),
@@ -55,6 +56,17 @@ _SIGS = {
     "phos_harness_digest": (_i32, [_vp, _vp, _u32, _vp, _vp]),
     "phos_harness_mutate": (_i32, [_vp, _u64, _u64, _vp, _u32, _vp, _u32, _vp, _u32, _vp]),
     "phos_harness_fill": (_i32, [_u64, _u64, _u64, _vp]),
+    "phos_plan_create": (_i32, [_vp, _u32, _P(_vp)]),
+    "phos_plan_launch": (_i32, [_vp, _vp]),
+    "phos_plan_set_tile": (_i32, [_vp, _u64]),
+    "phos_plan_autotune": (_i32, [_vp, _vp, _P(_u64), _P(_c.c_float)]),
+    "phos_plan_info": (_i32, [_vp, _P(_u64), _P(_u64), _P(_u64), _P(_u32)]),
+    "phos_plan_destroy": (_i32, [_vp]),
+    "phos_server_start": (_i32, [_vp, _P(_vp)]),
+    "phos_server_submit": (_i32, [_vp, _vp, _P(_u64)]),
+    "phos_server_poll": (_i32, [_vp, _u64, _vp]),
+    "phos_server_drain": (_i32, [_vp, _u32]),
+    "phos_server_stop": (_i32, [_vp]),
     "phos_ckpt_begin": (_i32, [_vp, _vp, _vp, _P(_vp)]),
     "phos_ckpt_advance": (_i32, [_vp, _u64, _P(_c.c_int)]),
     "phos_ckpt_before_kernel": (_i32, [_vp, _vp]),
@@ -74,6 +86,31 @@ _SIGS = {
 }
 
 CKPT_COW, CKPT_RECOPY = 1, 2
+
+
+REQ_CHECKPOINT, REQ_RESTORE = 1, 2
+
+
+class ServerDesc(_c.Structure):
+    _fields_ = [("max_slots", _u32), ("reserved", _u32), ("d_staging", _vp),
+                ("staging_bytes", _u64), ("chunk", _u64), ("dma_min", _u64)]
+
+
+class Request(_c.Structure):
+    _fields_ = [("kind", _u32), ("reserved", _u32), ("table", _vp), ("host", _vp),
+                ("host_bytes", _u64)]
+
+
+class Result(_c.Structure):
+    _fields_ = [("state", _u32), ("status", _i32), ("bytes", _u64), ("t_submit_ns", _u64),
+                ("t_admit_ns", _u64), ("t_done_ns", _u64)]
+
+
+class PlanItem(_c.Structure):
+    _fields_ = [("table", _vp), ("d_perm", _vp), ("d_trace", _vp), ("n_rec", _u64),
+                ("access_bytes", _u32), ("n_copy", _u32), ("d_bitmap", _vp), ("d_count", _vp),
+                ("d_victim", _vp), ("d_victim_st", _vp), ("d_list", _vp), ("staging", _vp),
+                ("staging_bytes", _u64), ("image", _vp), ("image_bytes", _u64)]
 
 
 class CkptDesc(_c.Structure):
@@ -241,6 +278,10 @@ def validate_config(variant=0):
     return check(lib().phos_validate_config(variant), "validate_config")
 
 
+def host_copy_config(dma_min_bytes=0):
+    return check(lib().phos_host_copy_config(dma_min_bytes), "host_copy_config")
+
+
 def copy_config(tile_bytes=0, ctas_per_sm=0):
     return check(lib().phos_copy_config(tile_bytes, ctas_per_sm), "copy_config")
 
@@ -363,6 +404,80 @@ class Restore:
     def close(self):
         if self.h:
             lib().phos_restore_end(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Batched plan (phos_plan_*): many items, one persistent graph launch."""
+
+    def __init__(self, items):
+        arr = (PlanItem * max(len(items), 1))(*items)
+        h = _vp()
+        check(lib().phos_plan_create(_c.cast(arr, _vp), len(items), _c.byref(h)), "plan_create")
+        self.h = h.value
+
+    def launch(self, stream=None):
+        check(lib().phos_plan_launch(self.h, stream), "plan_launch")
+
+    def set_tile(self, tile):
+        check(lib().phos_plan_set_tile(self.h, tile), "plan_set_tile")
+
+    def autotune(self, stream=None):
+        t, ms = _u64(), _c.c_float()
+        check(lib().phos_plan_autotune(self.h, stream, _c.byref(t), _c.byref(ms)),
+              "plan_autotune")
+        return int(t.value), float(ms.value)
+
+    def info(self):
+        r, b, t, st = _u64(), _u64(), _u64(), _u32()
+        check(lib().phos_plan_info(self.h, _c.byref(r), _c.byref(b), _c.byref(t), _c.byref(st)),
+              "plan_info")
+        return dict(records=r.value, copy_bytes=b.value, tile=t.value, status=st.value)
+
+    def close(self):
+        if self.h:
+            lib().phos_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (phos_server_*)."""
+
+    def __init__(self, max_slots, d_staging, staging_bytes, chunk=4 << 20, dma_min=1 << 20):
+        d = ServerDesc(max_slots, 0, d_staging, staging_bytes, chunk, dma_min)
+        h = _vp()
+        check(lib().phos_server_start(_c.byref(d), _c.byref(h)), "server_start")
+        self.h = h.value
+
+    def submit(self, kind, table, host, host_bytes):
+        r = Request(kind, 0, table.handle, host, host_bytes)
+        t = _u64()
+        check(lib().phos_server_submit(self.h, _c.byref(r), _c.byref(t)), "server_submit")
+        return int(t.value)
+
+    def poll(self, ticket):
+        r = Result()
+        check(lib().phos_server_poll(self.h, ticket, _c.byref(r)), "server_poll")
+        return {f: getattr(r, f) for f, _ in r._fields_}
+
+    def drain(self, timeout_ms=600_000):
+        check(lib().phos_server_drain(self.h, timeout_ms), "server_drain")
+
+    def close(self):
+        if self.h:
+            lib().phos_server_stop(self.h)
             self.h = None
 
     def __del__(self):

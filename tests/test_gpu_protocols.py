@@ -14,6 +14,15 @@ from oracle import protocols as P  # noqa: E402
 from paper_2405_12079_b300 import phos, runner, workloads as wl  # noqa: E402
 
 
+@pytest.fixture(autouse=True, params=[0, 16384], ids=["sm-copies", "dma-host-legs"])
+def host_legs(request):
+    """Every protocol case runs with the host legs on the SM copy kernel and
+    with pieces of >= 16 KiB on the DMA engines; results must not change."""
+    phos.host_copy_config(request.param)
+    yield request.param
+    phos.host_copy_config(0)
+
+
 def a256(x):
     return (int(x) + 255) // 256 * 256
 
