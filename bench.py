@@ -107,6 +107,22 @@ def run_reference(args, rank, world):
 
 # --------------------------------------------------------------- GPU arm
 
+def across_ranks(ms, moved, recs, world):
+    """Replicas: the job's time is the slowest rank's, its work the sum of
+    every rank's (host-side bookkeeping only; no collective touches the
+    data path).  Works on any process-group backend."""
+    if world <= 1:
+        return ms, moved, recs
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    v = torch.tensor([moved, recs], dtype=torch.float64, device=dev)
+    dist.all_reduce(v)
+    return float(t.item()), int(v[0].item()), int(v[1].item())
+
+
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -284,15 +300,7 @@ def run_gpu(args, rank, world):
     clocks = clk.stop()
     marks.collect(phase)
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    tot_moved, tot_recs = moved, recs
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        v = torch.tensor([moved, recs], dtype=torch.float64, device="cuda")
-        dist.all_reduce(v)
-        tot_moved, tot_recs = int(v[0].item()), int(v[1].item())
+    t_max, tot_moved, tot_recs = across_ranks(ms, moved, recs, world)
 
     # per-kernel rooflines from the same run
     pk = peaks()
@@ -633,6 +641,7 @@ def run_serving(args, rank, world):
 
         def feeder():
             try:
+                torch.cuda.set_device(dev)
                 for i, (t, hp, ib, kind, ta) in enumerate(tables):
                     delay = t0 + int(ta * 1e9) - time.monotonic_ns()
                     if delay > 0:

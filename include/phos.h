@@ -294,8 +294,8 @@ phos_status phos_plan_destroy(phos_plan_t *p);
  * (a checkpoint needs staging for its whole image, a restore none, so a
  * restore may pass a checkpoint that waits), snapshots checkpoints into
  * staging at HBM speed, and moves every admitted request's host leg in
- * pieces, round-robin across requests, device->host and host->device at
- * the same time.  Pieces of >= dma_min bytes go to the DMA engines, smaller
+ * pieces, oldest request first, device->host and host->device at the same
+ * time.  Pieces of >= dma_min bytes go to the DMA engines, smaller
  * ones to the SM copy kernel.  Requests must be independent: no two
  * requests in flight may share a table handle or overlapping memory. */
 

@@ -1,0 +1,432 @@
+// Serving loop: continuous batching of checkpoint and restore requests
+// (the restore-mostly serverless case of PhoenixOS Sec. 7 "Fast GPU
+// serverless function startups", and periodic checkpoints of Sec. 7
+// "Fault tolerance", served as a stream of requests).
+//
+// A scheduler thread owns three streams: device->device snapshots,
+// device->host drains and host->device loads.  Requests are admitted, in
+// arrival order where possible, as slots and staging budget free up (a
+// checkpoint needs staging for its whole image; a restore needs none, so
+// it may pass a checkpoint that waits for staging).  A checkpoint is
+// snapshotted into staging with one copy-engine launch (HBM speed), then
+// drained to its pinned host image in pieces; a restore is loaded piece by
+// piece.  Each scheduling turn fills one batch per direction (up to 64 MB,
+// at most two batches queued per direction) with pieces of the admitted
+// requests, oldest first, so a request that arrives while others are on the
+// GPU joins the next batch that has room, and the two directions run
+// concurrently.  Completion is tracked with events; no turn blocks on the
+// device.
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace phos {
+
+static uint64_t now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (uint64_t)ts.tv_sec * 1000000000ull + (uint64_t)ts.tv_nsec;
+}
+
+struct Req {
+    uint64_t ticket;
+    phos_request_t r;
+    phos_result_t res;
+    // progress
+    uint64_t stg_off = 0;          // checkpoint: staging extent
+    uint64_t img_bytes = 0;
+    uint64_t issued = 0;           // host-leg bytes issued
+    uint32_t buf = 0;              // restore: next buffer / offset
+    uint64_t buf_off = 0;
+    bool snap_done = false;
+    cudaEvent_t snap_ev = nullptr;
+    cudaEvent_t last_ev = nullptr; // event after the request's last piece
+};
+
+// One batch issued on a host-leg stream.
+struct Issue {
+    cudaEvent_t ev;
+    std::vector<uint64_t> finishing;  // tickets whose last piece is in this batch
+};
+
+}  // namespace phos
+
+using namespace phos;
+
+struct phos_server {
+    phos_server_desc_t d{};
+    int device = 0;
+    cudaStream_t s_snap = nullptr, s_d2h = nullptr, s_h2d = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::deque<uint64_t> queue;                 // submitted, not admitted
+    std::map<uint64_t, Req> reqs;               // all requests by ticket
+    std::vector<uint64_t> active;               // admitted, not done
+    std::vector<std::pair<uint64_t, uint64_t>> free_stg;  // staging extents
+    std::deque<Issue> inflight_d2h, inflight_h2d;
+    std::vector<cudaEvent_t> ev_pool;
+    // device descriptor rings per direction (pinned staging of lists)
+    phos_copy_t *h_ring[3] = {nullptr, nullptr, nullptr};
+    phos_copy_t *d_ring[3] = {nullptr, nullptr, nullptr};
+    uint32_t *d_status = nullptr;
+    size_t ring_cap = 65536;
+    size_t ring_pos[3] = {0, 0, 0};
+    std::atomic<uint64_t> busy_turns{0};
+    phos_status err = PHOS_OK;
+
+    cudaEvent_t get_ev() {
+        if (!ev_pool.empty()) {
+            cudaEvent_t e = ev_pool.back();
+            ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        return e;
+    }
+
+    bool stg_alloc(uint64_t need, uint64_t *off) {
+        for (size_t j = 0; j < free_stg.size(); ++j)
+            if (free_stg[j].second >= need) {
+                *off = free_stg[j].first;
+                if (free_stg[j].second == need)
+                    free_stg.erase(free_stg.begin() + j);
+                else
+                    free_stg[j] = {free_stg[j].first + need, free_stg[j].second - need};
+                return true;
+            }
+        return false;
+    }
+    void stg_release(uint64_t off, uint64_t len) {
+        auto it = std::lower_bound(free_stg.begin(), free_stg.end(),
+                                   std::make_pair(off, (uint64_t)0));
+        it = free_stg.insert(it, {off, len});
+        size_t j = it - free_stg.begin();
+        if (j + 1 < free_stg.size() && free_stg[j].first + free_stg[j].second == free_stg[j + 1].first) {
+            free_stg[j].second += free_stg[j + 1].second;
+            free_stg.erase(free_stg.begin() + j + 1);
+        }
+        if (j > 0 && free_stg[j - 1].first + free_stg[j - 1].second == free_stg[j].first) {
+            free_stg[j - 1].second += free_stg[j].second;
+            free_stg.erase(free_stg.begin() + j);
+        }
+    }
+
+    // Copy descriptors through the copy engine on stream s.  Lists go
+    // through ring r of pinned + device memory; before the ring wraps, the
+    // stream is synchronised so no list is overwritten before its upload.
+    phos_status launch(int r, cudaStream_t s, const phos_table_t *t,
+                       const std::vector<phos_copy_t> &v, void *img, uint64_t img_bytes) {
+        if (v.empty()) return PHOS_OK;
+        if (v.size() > ring_cap) return fail(PHOS_EINVAL, "server: batch of %zu pieces", v.size());
+        if (ring_pos[r] + v.size() > ring_cap) {
+            PHOS_CUDA(cudaStreamSynchronize(s));
+            ring_pos[r] = 0;
+        }
+        phos_copy_t *hp = h_ring[r] + ring_pos[r];
+        phos_copy_t *dp = d_ring[r] + ring_pos[r];
+        memcpy(hp, v.data(), v.size() * sizeof(phos_copy_t));
+        PHOS_CUDA(cudaMemcpyAsync(dp, hp, v.size() * sizeof(phos_copy_t), cudaMemcpyHostToDevice,
+                                  s));
+        ring_pos[r] += v.size();
+        return phos_copy(t, dp, (uint32_t)v.size(), d.d_staging, d.staging_bytes, img, img_bytes,
+                         nullptr, d_status, s);
+    }
+
+    void admit() {
+        for (auto it = queue.begin(); it != queue.end() && active.size() < d.max_slots;) {
+            Req &q = reqs[*it];
+            const phos_table *t = q.r.table;
+            q.img_bytes = t->image_bytes;
+            if (q.r.kind == PHOS_REQ_CHECKPOINT && q.img_bytes) {
+                uint64_t off;
+                if (!stg_alloc(align_up(q.img_bytes, 256), &off)) {
+                    ++it;                      // waits for staging; restores may pass
+                    if (d.max_slots == 1) break;
+                    continue;
+                }
+                q.stg_off = off;
+                // snapshot: every buffer live -> staging at its image offset
+                std::vector<phos_copy_t> v(t->n);
+                for (uint32_t i = 0; i < t->n; ++i)
+                    v[i] = phos_copy_t{0, off + t->img_off[i], t->size[i], i,
+                                       PHOS_COPY_LIVE_TO_STAGING};
+                phos_status e = launch(0, s_snap, t, v, nullptr, 0);
+                q.snap_ev = get_ev();
+                cudaEventRecord(q.snap_ev, s_snap);
+                if (e) q.res.status = e;
+            }
+            q.res.state = 1;
+            q.res.t_admit_ns = now_ns();
+            active.push_back(q.ticket);
+            it = queue.erase(it);
+        }
+    }
+
+    // One host-leg batch for a direction: pieces of the admitted requests of
+    // that direction, oldest first, up to `batch` bytes.
+    void issue(bool d2h) {
+        std::deque<Issue> &inf = d2h ? inflight_d2h : inflight_h2d;
+        if (inf.size() >= 2) return;           // keep at most two batches queued
+        const uint64_t batch = std::max<uint64_t>(d.chunk * 8, 64ull << 20);
+        std::vector<Req *> cand;
+        for (uint64_t tk : active) {
+            Req &q = reqs[tk];
+            if (q.res.state != 1 || q.res.status) continue;
+            if (d2h && q.r.kind == PHOS_REQ_CHECKPOINT && q.issued < q.img_bytes) {
+                if (!q.snap_done) {
+                    if (cudaEventQuery(q.snap_ev) != cudaSuccess) continue;
+                    q.snap_done = true;
+                }
+                cand.push_back(&q);
+            } else if (!d2h && q.r.kind == PHOS_REQ_RESTORE && q.issued < q.img_bytes) {
+                cand.push_back(&q);
+            }
+        }
+        if (cand.empty()) return;
+        Issue is;
+        uint64_t used = 0, pieces = 0;
+        std::vector<std::vector<phos_copy_t>> lists(cand.size());
+        // oldest admitted request first: a batch takes its pieces, then the
+        // next request's, so small requests behind a large one still start
+        // as soon as the large one's remaining bytes fit in a batch, and
+        // the other direction is never held up
+        for (size_t c = 0; c < cand.size() && used < batch && pieces < 1024; ++c) {
+            Req &q = *cand[c];
+            const phos_table *t = q.r.table;
+            while (q.issued < q.img_bytes && used < batch && pieces < 1024) {
+                // pieces of the next buffer with bytes left (never across a
+                // buffer, so the image's padding is left alone)
+                while (q.buf < t->n && q.buf_off >= t->size[q.buf]) {
+                    ++q.buf;
+                    q.buf_off = 0;
+                }
+                if (q.buf < t->n) {
+                    const uint64_t take = std::min(d.chunk, t->size[q.buf] - q.buf_off);
+                    const uint64_t io = t->img_off[q.buf] + q.buf_off;
+                    if (d2h)        // staging holds the image layout
+                        lists[c].push_back(phos_copy_t{q.stg_off + io, io, take, q.buf,
+                                                       PHOS_COPY_STAGING_TO_IMAGE});
+                    else
+                        lists[c].push_back(phos_copy_t{io, q.buf_off, take, q.buf,
+                                                       PHOS_COPY_IMAGE_TO_LIVE});
+                    q.buf_off += take;
+                    used += take;
+                    ++pieces;
+                }
+                while (q.buf < t->n && q.buf_off >= t->size[q.buf]) {
+                    ++q.buf;
+                    q.buf_off = 0;
+                }
+                if (q.buf >= t->n) {
+                    q.issued = q.img_bytes;
+                    is.finishing.push_back(q.ticket);
+                }
+            }
+        }
+        cudaStream_t s = d2h ? s_d2h : s_h2d;
+        for (size_t c = 0; c < cand.size(); ++c) {
+            if (lists[c].empty()) continue;
+            Req &q = *cand[c];
+            std::vector<phos_copy_t> kern;
+            for (const phos_copy_t &p : lists[c]) {
+                if (d.dma_min && p.len >= d.dma_min) {
+                    const phos_table *t = q.r.table;
+                    const uint8_t *src;
+                    uint8_t *dst;
+                    if (d2h) {
+                        src = static_cast<const uint8_t *>(d.d_staging) + p.src_off;
+                        dst = static_cast<uint8_t *>(q.r.host) + p.dst_off;
+                    } else {
+                        src = static_cast<const uint8_t *>(q.r.host) + p.src_off;
+                        dst = reinterpret_cast<uint8_t *>(t->base[p.buf] + p.dst_off);
+                    }
+                    cudaError_t ce = cudaMemcpyAsync(dst, src, p.len, cudaMemcpyDefault, s);
+                    if (ce != cudaSuccess) q.res.status = PHOS_ECUDA;
+                } else {
+                    kern.push_back(p);
+                }
+            }
+            phos_status e = launch(d2h ? 1 : 2, s, q.r.table, kern, q.r.host, q.r.host_bytes);
+            if (e) q.res.status = e;
+        }
+        is.ev = get_ev();
+        cudaEventRecord(is.ev, s);
+        inf.push_back(std::move(is));
+    }
+
+    void retire(std::deque<Issue> &inf) {
+        while (!inf.empty() && cudaEventQuery(inf.front().ev) == cudaSuccess) {
+            Issue &is = inf.front();
+            const uint64_t t = now_ns();
+            for (uint64_t tk : is.finishing) {
+                Req &q = reqs[tk];
+                q.res.state = q.res.status ? 3 : 2;
+                q.res.t_done_ns = t;
+                q.res.bytes = q.img_bytes;
+                if (q.r.kind == PHOS_REQ_CHECKPOINT && q.img_bytes)
+                    stg_release(q.stg_off, align_up(q.img_bytes, 256));
+                if (q.snap_ev) ev_pool.push_back(q.snap_ev);
+                q.snap_ev = nullptr;
+                active.erase(std::find(active.begin(), active.end(), tk));
+            }
+            ev_pool.push_back(is.ev);
+            inf.pop_front();
+        }
+    }
+
+    void loop() {
+        cudaSetDevice(device);
+        std::unique_lock<std::mutex> lk(mu);
+        while (true) {
+            retire(inflight_d2h);
+            retire(inflight_h2d);
+            admit();
+            issue(true);
+            issue(false);
+            // empty restores / zero-byte checkpoints complete at once
+            for (size_t k = 0; k < active.size();) {
+                Req &q = reqs[active[k]];
+                if (q.img_bytes == 0 && q.res.state == 1) {
+                    q.res.state = 2;
+                    q.res.t_done_ns = now_ns();
+                    active.erase(active.begin() + k);
+                } else {
+                    ++k;
+                }
+            }
+            if (stop && queue.empty() && active.empty()) break;
+            const bool idle = queue.empty() && active.empty();
+            if (idle) {
+                cv.wait_for(lk, std::chrono::milliseconds(5));
+            } else {
+                lk.unlock();
+                std::this_thread::sleep_for(std::chrono::microseconds(20));
+                lk.lock();
+            }
+        }
+    }
+};
+
+extern "C" phos_status phos_server_start(const phos_server_desc_t *d, phos_server_t **out) {
+    if (!d || !out) return fail(PHOS_EINVAL, "server_start: NULL argument");
+    *out = nullptr;
+    if (d->max_slots == 0 || d->chunk == 0 || d->chunk % 256)
+        return fail(PHOS_EINVAL, "server_start: max_slots >= 1, chunk a multiple of 256");
+    if (d->staging_bytes && !d->d_staging)
+        return fail(PHOS_EINVAL, "server_start: staging budget without a staging area");
+    phos_server *S = new phos_server();
+    S->d = *d;
+    cudaGetDevice(&S->device);
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&S->s_snap, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&S->s_d2h, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&S->s_h2d, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaMalloc(&S->d_status, 256)) != cudaSuccess ||
+        (e = cudaMemset(S->d_status, 0, 256)) != cudaSuccess) {
+        delete S;
+        return cuda_fail(e, "server_start");
+    }
+    for (int r = 0; r < 3; ++r) {
+        if ((e = cudaHostAlloc(&S->h_ring[r], S->ring_cap * sizeof(phos_copy_t),
+                               cudaHostAllocDefault)) != cudaSuccess ||
+            (e = cudaMalloc(&S->d_ring[r], S->ring_cap * sizeof(phos_copy_t))) != cudaSuccess) {
+            delete S;
+            return cuda_fail(e, "server_start: rings");
+        }
+    }
+    if (d->staging_bytes) S->free_stg.push_back({0, d->staging_bytes});
+    S->th = std::thread([S] { S->loop(); });
+    *out = S;
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_server_submit(phos_server_t *S, const phos_request_t *r,
+                                          uint64_t *ticket) {
+    if (!S || !r || !r->table || !ticket) return fail(PHOS_EINVAL, "server_submit: NULL argument");
+    if (r->kind != PHOS_REQ_CHECKPOINT && r->kind != PHOS_REQ_RESTORE)
+        return fail(PHOS_EINVAL, "server_submit: kind %u", r->kind);
+    if (r->host_bytes < r->table->image_bytes || (!r->host && r->table->image_bytes))
+        return fail(PHOS_EINVAL, "server_submit: host image smaller than the table's image");
+    // callers may submit from any thread: bind the server's device first
+    PHOS_CUDA(cudaSetDevice(S->device));
+    void *dv = nullptr;
+    phos_status st = device_view(r->host, &dv);
+    if (st) return st;
+    if (r->kind == PHOS_REQ_CHECKPOINT && align_up(r->table->image_bytes, 256) > S->d.staging_bytes)
+        return fail(PHOS_EBUDGET, "server_submit: image of %llu bytes exceeds the staging budget",
+                    (unsigned long long)r->table->image_bytes);
+    std::lock_guard<std::mutex> g(S->mu);
+    Req q;
+    q.ticket = S->next_ticket++;
+    q.r = *r;
+    q.r.host = dv;
+    memset(&q.res, 0, sizeof q.res);
+    q.res.t_submit_ns = now_ns();
+    S->reqs[q.ticket] = q;
+    S->queue.push_back(q.ticket);
+    *ticket = q.ticket;
+    S->cv.notify_one();
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_server_poll(phos_server_t *S, uint64_t ticket, phos_result_t *out) {
+    if (!S || !out) return fail(PHOS_EINVAL, "server_poll: NULL argument");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(PHOS_EINVAL, "server_poll: unknown ticket");
+    *out = it->second.res;
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_server_drain(phos_server_t *S, uint32_t timeout_ms) {
+    if (!S) return fail(PHOS_EINVAL, "server_drain: NULL server");
+    const uint64_t t_end = now_ns() + (uint64_t)timeout_ms * 1000000ull;
+    while (true) {
+        {
+            std::lock_guard<std::mutex> g(S->mu);
+            if (S->queue.empty() && S->active.empty()) return PHOS_OK;
+        }
+        if (now_ns() > t_end) return fail(PHOS_ETIMEDOUT, "server_drain: timed out");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
+extern "C" phos_status phos_server_stop(phos_server_t *S) {
+    if (!S) return PHOS_OK;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+        S->cv.notify_one();
+    }
+    S->th.join();
+    cudaStreamSynchronize(S->s_snap);
+    cudaStreamSynchronize(S->s_d2h);
+    cudaStreamSynchronize(S->s_h2d);
+    for (auto &kv : S->reqs)
+        if (kv.second.snap_ev) cudaEventDestroy(kv.second.snap_ev);
+    for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
+    for (int r = 0; r < 3; ++r) {
+        cudaFreeHost(S->h_ring[r]);
+        cudaFree(S->d_ring[r]);
+    }
+    cudaFree(S->d_status);
+    cudaStreamDestroy(S->s_snap);
+    cudaStreamDestroy(S->s_d2h);
+    cudaStreamDestroy(S->s_h2d);
+    delete S;
+    return PHOS_OK;
+}

@@ -75,6 +75,23 @@ def bench_validate(K, out, variants=(1, 2)):
                                                 gbs=n1 * 8.125 / ms / 1e6)
         ms = timeit(lambda: run(rrd.data_ptr(), len(rr)))
         out["validate_random_" + tag] = dict(records=len(rr), ms=ms, grec_s=len(rr) / ms / 1e6)
+        # the per-trace launches replayed from a CUDA graph: device time
+        # without the host's per-call overhead
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            run(big.data_ptr(), n1)                  # warm scratch outside capture
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=cs):
+                for j in range(K):
+                    phos.validate(t, d_perm.data_ptr(), big.data_ptr() + 8 * n1 * j, n1, 4,
+                                  bm.data_ptr(), cnt.data_ptr(), vv.data_ptr(),
+                                  vv.data_ptr() + 128, None, 0, st.data_ptr(),
+                                  cs.cuda_stream)
+        ms = timeit(lambda: g.replay(), 3, 1) / K
+        out["validate_per_trace_graph_" + tag] = dict(records=n1, us=1e3 * ms,
+                                                      grec_s=n1 / ms / 1e6)
     phos.validate_config(0)
 
 

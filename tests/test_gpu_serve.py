@@ -1,0 +1,120 @@
+"""The serving loop: every checkpoint and restore request gives the same
+bytes alone (one at a time) and in the mix (continuous batching), and those
+bytes are what the oracle's memcpy gives; admission waits for the staging
+budget instead of failing."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import copyeng  # noqa: E402
+from paper_2405_12079_b300 import phos, workloads as wl  # noqa: E402
+
+
+def a256(x):
+    return (int(x) + 255) // 256 * 256
+
+
+class World:
+    """Disjoint device and host regions, one per request."""
+
+    def __init__(self, seed, n_req=24):
+        rng = np.random.default_rng(seed)
+        self.rng = rng
+        self.dev_h = rng.integers(0, 256, 96 << 20, dtype=np.uint8)
+        self.host_h = rng.integers(0, 256, 96 << 20, dtype=np.uint8)
+        self.dev = torch.from_numpy(self.dev_h.copy()).cuda()
+        self.host = torch.from_numpy(self.host_h.copy()).pin_memory()
+        self.reqs = []
+        doff = hoff = 0
+        for q in range(n_req):
+            nb = int(rng.integers(1, 300))
+            sizes = wl.sizes_uniform(rng, nb, 1, int(rng.integers(2_000, 60_000)))
+            lay = wl.make_layout(rng, sizes, gap_lo=0, gap_hi=2048)
+            off = doff
+            doff += lay.arena_bytes + 4096
+            t = phos.Table(lay.base(self.dev.data_ptr() + off), lay.size)
+            img = t.image_bytes()
+            kind = phos.REQ_CHECKPOINT if q % 2 == 0 else phos.REQ_RESTORE
+            self.reqs.append(dict(kind=kind, lay=lay, dev_off=off, table=t, host_off=hoff,
+                                  img=img, img_off=t.image_offsets()))
+            hoff += a256(img) + 4096
+        assert doff <= self.dev_h.size and hoff <= self.host_h.size
+
+    def reset(self):
+        self.dev.copy_(torch.from_numpy(self.dev_h))
+        self.host.copy_(torch.from_numpy(self.host_h))
+        torch.cuda.synchronize()
+
+    def expected(self):
+        dev, host = self.dev_h.copy(), self.host_h.copy()
+        for r in self.reqs:
+            lay, n = r["lay"], r["lay"].n
+            d = np.zeros(n, copyeng.DESC_DTYPE)
+            for i in range(n):
+                if r["kind"] == phos.REQ_CHECKPOINT:
+                    d[i] = (0, r["host_off"] + int(r["img_off"][i]), int(lay.size[i]), i,
+                            copyeng.LIVE_TO_IMAGE)
+                else:
+                    d[i] = (r["host_off"] + int(r["img_off"][i]), 0, int(lay.size[i]), i,
+                            copyeng.IMAGE_TO_LIVE)
+            assert copyeng.apply(d, dev, lay.off + np.uint64(r["dev_off"]), lay.size,
+                                 image=host) == 0
+        return dev, host
+
+    def submit(self, srv, r):
+        return srv.submit(r["kind"], r["table"], self.host.data_ptr() + r["host_off"],
+                          a256(r["img"]))
+
+
+@pytest.mark.parametrize("dma_min", [0, 256 << 10], ids=["sm-copies", "dma"])
+def test_alone_and_mix_give_the_same_bytes(dma_min):
+    w = World(5)
+    exp_dev, exp_host = w.expected()
+    cks = [a256(r["img"]) for r in w.reqs if r["kind"] == phos.REQ_CHECKPOINT]
+    stg = max(max(cks), sum(cks) // 2)       # smaller than all checkpoints together
+    staging = torch.empty(stg, dtype=torch.uint8, device="cuda")
+
+    # alone: one request at a time
+    w.reset()
+    srv = phos.Server(1, staging.data_ptr(), staging.numel(), chunk=64 << 10, dma_min=dma_min)
+    for r in w.reqs:
+        tk = w.submit(srv, r)
+        srv.drain(60_000)
+        res = srv.poll(tk)
+        assert res["state"] == 2 and res["status"] == 0
+    srv.close()
+    torch.cuda.synchronize()
+    assert np.array_equal(w.dev.cpu().numpy(), exp_dev)
+    assert np.array_equal(w.host.numpy(), exp_host)
+
+    # mix: continuous batching, arrivals while others are in flight, a
+    # staging budget smaller than the checkpoints' total
+    w.reset()
+    srv = phos.Server(8, staging.data_ptr(), staging.numel(), chunk=64 << 10, dma_min=dma_min)
+    tks = []
+    for r in w.reqs:
+        tks.append(w.submit(srv, r))
+        time.sleep(float(w.rng.exponential(0.0005)))
+    srv.drain(60_000)
+    res = [srv.poll(t) for t in tks]
+    srv.close()
+    torch.cuda.synchronize()
+    assert all(x["state"] == 2 and x["status"] == 0 for x in res)
+    assert all(x["t_done_ns"] >= x["t_admit_ns"] >= x["t_submit_ns"] for x in res)
+    assert np.array_equal(w.dev.cpu().numpy(), exp_dev)
+    assert np.array_equal(w.host.numpy(), exp_host)
+    assert sum(cks) > staging.numel()    # admission had to wait for budget
+
+
+def test_request_larger_than_budget_is_refused():
+    w = World(6, n_req=2)
+    staging = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    srv = phos.Server(4, staging.data_ptr(), staging.numel())
+    with pytest.raises(phos.PhosError) as e:
+        w.submit(srv, w.reqs[0])
+    assert e.value.code == phos.PHOS_EBUDGET
+    srv.close()
