@@ -48,7 +48,6 @@ cases (zero staging budget, zero kernels, copier faster than the kernels).
 import numpy as np
 
 from . import core
-from . import copyeng
 
 PENDING, INFLIGHT, DONE = 0, 1, 2
 PERM_R, PERM_W = 1, 2

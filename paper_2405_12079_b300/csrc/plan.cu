@@ -158,9 +158,9 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(const PlanDev P) {
             __syncwarp();
             uint32_t *bm = it.bitmap + (r0 >> 5);
             if (nb == kBatch)
-                batch_words<true, true>(L, recs, nb, lane, mine, bm, sv, svs, acc);
+                batch_words<true, true>(L, recs, nb, 32, lane, mine, bm, sv, svs, acc);
             else
-                batch_words<true, false>(L, recs, nb, lane, mine, bm, sv, svs, acc);
+                batch_words<true, false>(L, recs, nb, 32, lane, mine, bm, sv, svs, acc);
             __syncwarp();
         }
         if (__any_sync(0xffffffffu, acc.bad) && lane == 0) s_misc[1] = 1;

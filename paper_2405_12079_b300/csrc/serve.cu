@@ -20,7 +20,6 @@
 #include <time.h>
 
 #include <algorithm>
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -50,7 +49,6 @@ struct Req {
     uint64_t buf_off = 0;
     bool snap_done = false;
     cudaEvent_t snap_ev = nullptr;
-    cudaEvent_t last_ev = nullptr; // event after the request's last piece
 };
 
 // One batch issued on a host-leg stream.
@@ -84,8 +82,6 @@ struct phos_server {
     uint32_t *d_status = nullptr;
     size_t ring_cap = 65536;
     size_t ring_pos[3] = {0, 0, 0};
-    std::atomic<uint64_t> busy_turns{0};
-    phos_status err = PHOS_OK;
 
     cudaEvent_t get_ev() {
         if (!ev_pool.empty()) {

@@ -61,6 +61,7 @@ struct ValParams {
     uint32_t w;
     uint32_t nvw;
     uint32_t stages;
+    uint32_t wpb;       // batched variant: bitmap words per warp batch
 };
 
 // Classify the 32 records of one bitmap word (one per lane) and write the
@@ -371,13 +372,15 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     __syncthreads();
 
     const uint64_t G = gridDim.x, c = blockIdx.x;
-    const uint64_t nbatch = (p.n_rec + kBatch - 1) / kBatch;
+    const uint32_t W = p.wpb;
+    const uint64_t brec = 32ull * W;
+    const uint64_t nbatch = (p.n_rec + brec - 1) / brec;
     const uint64_t b0 = nbatch * c / G, b1 = nbatch * (c + 1) / G;
     Lead *mine = leads + 32 * warp;
     Acc acc;
     for (uint64_t bt = b0 + warp; bt < b1; bt += nwarps) {
-        const uint64_t r0 = bt * kBatch;
-        const uint64_t nb = min((uint64_t)kBatch, p.n_rec - r0);
+        const uint64_t r0 = bt * brec;
+        const uint64_t nb = min(brec, p.n_rec - r0);
         const uint64_t *recs = p.trace + r0;
         // leaders: lane j searches the first record of word j
         {
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
             ld.l = 0;
             ld.i = -1;
             ld.pm = 0;
-            if (lane * 32 < nb) {
+            if (lane < W && lane * 32 < nb) {
                 const uint64_t x = recs[lane * 32] & PHOS_REC_ADDR_MASK;
                 const int i = L.lane_search(x);
                 if (i >= 0) {
@@ -400,10 +403,10 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         }
         __syncwarp();
         uint32_t *bm = p.bitmap + (r0 >> 5);
-        if (nb == kBatch)
-            batch_words<kSmemTable, true>(L, recs, nb, lane, mine, bm, sv, svs, acc);
+        if (nb == brec)
+            batch_words<kSmemTable, true>(L, recs, nb, W, lane, mine, bm, sv, svs, acc);
         else
-            batch_words<kSmemTable, false>(L, recs, nb, lane, mine, bm, sv, svs, acc);
+            batch_words<kSmemTable, false>(L, recs, nb, W, lane, mine, bm, sv, svs, acc);
         __syncwarp();
     }
     if (__any_sync(0xffffffffu, acc.bad) && lane == 0) set_status(p.status, PHOS_EINVAL);
@@ -546,6 +549,16 @@ static size_t plan_batched(uint32_t n, int device, bool *smem_table) {
 
 static uint32_t g_val_variant = 0;  // 0 auto, 1 TMA ring, 2 batched leaders
 
+// Words per warp batch: 32 (most amortisation of the leader searches)
+// unless that leaves fewer than two batches per warp of the grid; then 16,
+// then 8, so small traces still occupy every warp.
+static uint32_t words_per_batch(uint64_t n_rec, uint64_t ctas) {
+    const uint64_t warps = ctas * (kValThreads / 32);
+    uint32_t W = 32;
+    while (W > 8 && (n_rec + 32ull * W - 1) / (32ull * W) < 2 * warps) W /= 2;
+    return W;
+}
+
 }  // namespace phos
 
 using namespace phos;
@@ -574,9 +587,10 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     phos_table *T = const_cast<phos_table *>(t);
     const uint32_t variant = g_val_variant == 0 ? 2u : g_val_variant;
-    const uint64_t unit = variant == 1 ? kTileRec : kBatch;
-    const uint64_t units = (n_rec + unit - 1) / unit;
     const int sms = sm_count(T->device);
+    const uint32_t wpb = words_per_batch(n_rec, (uint64_t)sms);
+    const uint64_t unit = variant == 1 ? kTileRec : 32ull * wpb;
+    const uint64_t units = (n_rec + unit - 1) / unit;
     const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms, units));
     const uint32_t nvw = (t->n + 31) / 32;
     const size_t off_vacc = 256, off_cnt = align_up(off_vacc + 8ull * std::max(nvw, 1u), 256);
@@ -604,6 +618,7 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     p.w = access_bytes;
     p.nvw = nvw;
     p.stages = 0;
+    p.wpb = wpb;
     static bool attr_done[4] = {false, false, false, false};
     auto attr = [&](const void *fn, int slot) -> phos_status {
         if (!attr_done[slot]) {
@@ -730,10 +745,11 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
     if (r) return r;
     uint8_t *sc = static_cast<uint8_t *>(scr);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const uint64_t units = (n_rec + kBatch - 1) / kBatch;
-    const uint64_t G = std::max<uint64_t>(
-        1, std::min<uint64_t>(std::min<uint64_t>((uint64_t)sm_count(t->device), kNoallocMaxCtas),
-                              units));
+    const uint64_t ctas =
+        std::min<uint64_t>((uint64_t)sm_count(t->device), kNoallocMaxCtas);
+    const uint32_t wpb = words_per_batch(n_rec, ctas);
+    const uint64_t units = (n_rec + 32ull * wpb - 1) / (32ull * wpb);
+    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>(ctas, units));
     const uint32_t nvw = (t->n + 31) / 32;
     ValParams p;
     p.tab = t->view;
@@ -752,6 +768,7 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
     p.w = access_bytes;
     p.nvw = nvw;
     p.stages = 0;
+    p.wpb = wpb;
     k_noalloc_clear<<<1, 256, 0, s>>>(sc, nvw);
     count_launch();
     PHOS_CUDA(cudaGetLastError());
@@ -769,7 +786,7 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
     count_launch();
     PHOS_CUDA(cudaGetLastError());
     if (d_idx && idx_cap && n_rec) {
-        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, units, kBatch / 32,
+        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, units, wpb,
                                                     p.cta_cnt, d_idx, idx_cap);
         count_launch();
         PHOS_CUDA(cudaGetLastError());

@@ -66,16 +66,17 @@ struct Acc {
     bool bad = false;
 };
 
-// Batched-leader variant.  A warp takes 1024 consecutive records (32
-// bitmap words) at a time.  Lane j loads the first record of word j and
-// runs its own binary search for it, so the 32 searches of a batch run in
+// Batched-leader variant.  A warp takes W consecutive bitmap words (32 * W
+// records, W = 32 for large traces, 16 or 8 for small ones so that every
+// warp gets work) at a time.  Lane j loads the first record of word j and
+// runs its own binary search for it, so the W searches of a batch run in
 // parallel across the lanes; the interval found for word j (base, limit,
 // permission) is parked in the warp's shared-memory slot.  Then, word by
 // word, every lane checks its record against that interval with one
 // unsigned compare (broadcast reads), lanes that miss run their own
-// search, and the batch's 32 bitmap words leave in one coalesced store.
-// Records stream straight from HBM into registers, eight words ahead.
-constexpr uint32_t kBatch = 1024;
+// search, and the batch's W bitmap words leave in one coalesced store.
+// Records stream straight from HBM into registers, four words ahead.
+constexpr uint32_t kBatch = 1024;   // records of a full 32-word batch
 
 struct Lead {
     uint64_t b, l;     // base and limit of word j's leader interval
@@ -83,63 +84,87 @@ struct Lead {
     uint32_t pm;       // its permission byte
 };
 
+// Classify one record against its word's leader interval.  The store bit
+// is cleared but the reserved bits are kept, so a malformed record lies
+// above the 57-bit space and can never fall inside an interval: it misses
+// and is sorted out on the (rare) fallback path.
 template <bool kSmemTable, bool kFull>
-__device__ __forceinline__ void batch_words(const Look &L, const uint64_t *recs, uint64_t nb,
-                                            uint32_t lane, const Lead *lead, uint32_t *bm,
-                                            uint32_t *sv, uint32_t *svs, Acc &acc) {
-    uint32_t myvw = 0;
-#pragma unroll 1
-    for (uint32_t j0 = 0; j0 < 32; j0 += 8) {
-        uint64_t r[8];
-#pragma unroll
-        for (uint32_t u = 0; u < 8; ++u) {
-            const uint32_t k = (j0 + u) * 32 + lane;
-            r[u] = (kFull || k < nb) ? recs[k] : 0ull;
-        }
-#pragma unroll
-        for (uint32_t u = 0; u < 8; ++u) {
-            const uint32_t j = j0 + u;
-            const bool valid = kFull || (j * 32 + lane) < nb;
-            const uint64_t rec = r[u];
-            const uint64_t a = rec & PHOS_REC_ADDR_MASK;
-            const uint32_t hi = (uint32_t)(rec >> 32);
-            const bool st = (int32_t)hi < 0;
-            const bool bad = (hi & 0x7E000000u) != 0;
-            const Lead ld = lead[j];
-            bool hit = valid && !bad && (a - ld.b) < ld.l;
-            int bi = ld.i;
-            uint32_t pm = ld.pm;
-            const bool miss = valid && !bad && !hit;
-            if (__ballot_sync(0xffffffffu, miss)) {
-                if (miss) {
-                    const int ii = L.lane_search(a);
-                    if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
-                        hit = true;
-                        bi = ii;
-                        pm = L.perm[ii];
-                    }
+__device__ __forceinline__ void one_word(const Look &L, uint64_t rec, bool valid, uint32_t j,
+                                         uint32_t lane, const Lead &ld, uint32_t &myvw,
+                                         uint32_t *sv, uint32_t *svs, Acc &acc) {
+    if (kFull) valid = true;
+    const uint64_t a = rec & ~PHOS_REC_STORE;
+    const uint32_t st = (uint32_t)(rec >> 63);
+    bool hit = valid && (a - ld.b) < ld.l;
+    int bi = ld.i;
+    uint32_t pm = ld.pm;
+    const bool miss = valid && !hit;
+    bool bad = false;
+    if (__ballot_sync(0xffffffffu, miss)) {
+        if (miss) {
+            bad = a > PHOS_REC_ADDR_MASK;
+            if (!bad) {
+                const int ii = L.lane_search(a);
+                if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
+                    hit = true;
+                    bi = ii;
+                    pm = L.perm[ii];
                 }
-            }
-            const bool viol = valid && !(hit && (pm & (st ? 2u : 1u)));
-            const uint32_t vw = __ballot_sync(0xffffffffu, viol);
-            myvw = (lane == j) ? vw : myvw;
-            if (vw) {
-                const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
-                const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
-                if (lane == 0) {
-                    acc.c0 += __popc(vw);
-                    acc.c1 += __popc(sw);
-                    acc.c2 += __popc(uw);
-                }
-                if (viol && hit) {
-                    atomicOr(&sv[bi >> 5], 1u << (bi & 31));
-                    if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
-                }
-                acc.bad |= bad;
             }
         }
     }
-    if (kFull || lane * 32 < nb) bm[lane] = myvw;
+    const bool viol = valid && !(hit && ((pm >> st) & 1u));
+    const uint32_t vw = __ballot_sync(0xffffffffu, viol);
+    myvw = (lane == j) ? vw : myvw;
+    if (vw) {
+        const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
+        const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
+        if (lane == 0) {
+            acc.c0 += __popc(vw);
+            acc.c1 += __popc(sw);
+            acc.c2 += __popc(uw);
+        }
+        if (viol && hit) {
+            atomicOr(&sv[bi >> 5], 1u << (bi & 31));
+            if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
+        }
+        acc.bad |= bad;
+    }
+}
+
+// The W words (W = 8, 16 or 32) of one batch, records loaded four words
+// ahead of use.  kFull: the batch holds 32 * W records.
+template <bool kSmemTable, bool kFull>
+__device__ __forceinline__ void batch_words(const Look &L, const uint64_t *recs, uint64_t nb,
+                                            uint32_t W, uint32_t lane, const Lead *lead,
+                                            uint32_t *bm, uint32_t *sv, uint32_t *svs,
+                                            Acc &acc) {
+    uint32_t myvw = 0;
+    uint64_t r[4], n[4];
+#pragma unroll
+    for (uint32_t u = 0; u < 4; ++u) {
+        const uint32_t k = u * 32 + lane;
+        r[u] = (kFull || k < nb) ? recs[k] : 0ull;
+    }
+#pragma unroll 1
+    for (uint32_t j0 = 0; j0 < W; j0 += 4) {
+        if (j0 + 4 < W) {
+#pragma unroll
+            for (uint32_t u = 0; u < 4; ++u) {
+                const uint32_t k = (j0 + 4 + u) * 32 + lane;
+                n[u] = (kFull || k < nb) ? recs[k] : 0ull;
+            }
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + u;
+            one_word<kSmemTable, kFull>(L, r[u], kFull || (j * 32 + lane) < nb, j, lane, lead[j],
+                                        myvw, sv, svs, acc);
+        }
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) r[u] = n[u];
+    }
+    if (lane < W && (kFull || lane * 32 < nb)) bm[lane] = myvw;
 }
 
 }  // namespace phos

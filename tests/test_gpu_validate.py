@@ -145,3 +145,16 @@ def test_full_size_training_kernel_trace():
     rec, cls, _ = wl.trace_runs(rng, lay, VA0, reads, writes, cfg["n_rec"], 0.001, 0.1)
     got, exp = check(t, base, lay.size, perm, rec, 4, idx_cap=4096)
     assert int(exp.count[0]) == int((cls >= wl.CLS_OTHER).sum())
+
+
+@pytest.mark.parametrize("n_rec", [5_000_003, 12_000_017])
+def test_large_traces_take_the_wide_batches(n_rec):
+    """Traces large enough for 16- and 32-word warp batches (the kernel
+    narrows batches for small traces so every warp gets work)."""
+    rng, lay, base, t = layout_table(64, 70, hi=1 << 20)
+    reads, writes = wl.pick_sets(rng, 64, 1, 20)
+    perm = np.zeros(64, np.uint8)
+    perm[reads] = phos.PERM_R
+    perm[writes] = phos.PERM_RW
+    rec, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, n_rec, 0.002, 0.3)
+    check(t, base, lay.size, perm, rec, 4, idx_cap=20_000)
