@@ -476,6 +476,43 @@ BATCHED = ("batched: 64 independent process images, 20-2,000 buffers each (log-u
            "tile 64 KB-4 MB) vs plain per-image launches")
 
 
+def oracle_batched_sample():
+    """The oracle on a bounded sample of the batched workload: eight images'
+    1.3M-record traces validated by linear scan, and 1 GB of CoW copies done
+    as memcpy (numpy slice assignment)."""
+    from oracle import core, copyeng
+    from paper_2405_12079_b300 import workloads as wl
+    cfg = wl.batched(scale=1.0)
+    rng = cfg["rng"]
+    va0 = 0x7F00_0000_0000
+    tv, nrec, nbuf = 0.0, 0, []
+    for lay in cfg["images"][:8]:
+        reads, writes = wl.pick_sets(rng, lay.n)
+        perm = np.zeros(lay.n, np.uint8)
+        perm[reads] = 1
+        perm[writes] = 3
+        tr, _, _ = wl.trace_runs(rng, lay, va0, reads, writes, 1_300_000, 0.001, 0.0)
+        t0 = time.perf_counter()
+        core.validate(lay.base(va0), lay.size, perm, tr, 4)
+        tv += time.perf_counter() - t0
+        nrec += len(tr)
+        nbuf.append(lay.n)
+    g = 1 << 30
+    live = np.ones(g, np.uint8)
+    stg = np.zeros(g, np.uint8)
+    d = np.zeros(256, copyeng.DESC_DTYPE)
+    for i in range(256):
+        d[i] = (i * (g // 256), i * (g // 256), g // 256, 0, copyeng.LIVE_TO_STAGING)
+    t0 = time.perf_counter()
+    copyeng.apply(d, live, np.array([0], np.uint64), np.array([g], np.uint64), staging=stg)
+    tc = time.perf_counter() - t0
+    return {"value": g / tc / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "validated_accesses_per_s": nrec / tv,
+            "sample": "8 images' 1.3M-record traces over their tables of %s buffers (linear "
+                      "scan, %.1f s) and 1 GB of live->staging copies as memcpy (%.2f s), "
+                      "single thread" % (nbuf, tv, tc)}
+
+
 def run_batched(args, rank, world):
     """Batched form: all images' validation and copies in one graph launch."""
     import torch
@@ -581,6 +618,7 @@ def run_batched(args, rank, world):
                          "algorithmic_bytes": alg},
             "status": info["status"], "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
+        line["cpu_baseline"] = oracle_batched_sample()
         print(json.dumps(line), flush=True)
     plan.close()
 
@@ -823,6 +861,71 @@ def run_restore(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_budget(args, rank, world):
+    """Staging-budget sweep of the soft CoW checkpoint (the paper's Fig. 18
+    question: how much on-device memory does CoW need?).  Per budget: the
+    time kernels wait for CoW copies (the cow phase: device staging copies,
+    or direct copies to the host image when staging is full) and the
+    checkpoint's total time."""
+    import torch
+    from paper_2405_12079_b300 import phos, runner, workloads as wl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(scale=args.scale, n_kernels=200)
+    rng, lay = cfg["rng"], cfg["layout"]
+    arena = torch.empty(lay.arena_bytes, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(arena.data_ptr(), lay.arena_bytes, cfg["seed"], s)
+    kernels = wl.make_training_kernels(rng, lay, arena.data_ptr(), 200, cfg["n_rec"], 0.001)
+    dp = runner.DeviceProcess(lay, arena, cfg["seed"], kernels)
+    del kernels
+    image = torch.empty(dp.image_bytes, dtype=torch.uint8).pin_memory()
+    top = a256(2e9 * args.scale)
+    staging = torch.empty(top, dtype=torch.uint8, device="cuda")
+    quota, chunk = a256(dp.image_bytes / 100), 4 << 20
+    marks = Marks(torch)
+    rows = []
+    for frac in (0.0, 0.125, 0.25, 0.5, 1.0):
+        budget = a256(top * frac) if frac else 0
+        for rep in range(2):                         # first run warms up
+            c = phos.Checkpoint(dp.table, phos.CKPT_COW, image.data_ptr(), image.numel(), chunk,
+                                4, staging.data_ptr() if budget else None, budget, s)
+            k = 0
+            while k < len(dp.kernels):
+                marks.mark("copier")
+                if c.advance(quota):
+                    break
+                pk = dp.kernels[k]
+                marks.mark("cow")
+                c.before_kernel(pk.speculate(dp.table, dp.perm))
+                marks.mark("app")
+                dp.run_kernel(k)
+                marks.mark("validate")
+                c.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
+                k += 1
+            marks.mark("finish")
+            c.finish()
+            marks.mark("end")
+            st = c.stats()
+            c.close()
+            ph = {}
+            marks.collect(ph)
+        rows.append({"staging_bytes": budget, "cow_stall_ms": ph.get("cow", 0.0),
+                     "checkpoint_ms": sum(ph.values()), "cow_bytes": st["cow_bytes"],
+                     "direct_bytes": st["direct_bytes"], "kernels": st["kernels"]})
+    base = rows[-1]["cow_stall_ms"] or 1e-9
+    for r in rows:
+        r["stall_vs_full_budget"] = r["cow_stall_ms"] / base
+    line = {"metric": METRIC, "value": rows[-1]["checkpoint_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": world, "steps": 1, "warmup": 1,
+            "data": "synthetic", "dtype": "u8",
+            "config": {"workload": "staging-budget sweep of the soft CoW checkpoint of the "
+                                   "training-process image (%.1f GB)" % (dp.image_bytes / 1e9)},
+            "sweep": rows}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -830,7 +933,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phos", choices=["phos", "reference"])
     ap.add_argument("--workload", default="training",
-                    choices=["training", "batched", "serving", "restore"],
+                    choices=["training", "batched", "serving", "restore", "budget"],
                     help="training: the headline checkpoint step; batched: the 64-image plan")
     ap.add_argument("--host-copy", default="dma", choices=["sm", "dma"],
                     help="host legs on the SM copy kernel, or pieces >= 1 MiB on the DMA engines")
@@ -854,6 +957,8 @@ def main():
         run_serving(args, rank, world)
     elif args.workload == "restore":
         run_restore(args, rank, world)
+    elif args.workload == "budget":
+        run_budget(args, rank, world)
     else:
         run_gpu(args, rank, world)
     if world > 1:

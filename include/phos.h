@@ -192,6 +192,9 @@ phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_t *d_perm,
  * one of 32 words, the warp checks all 32 words against them).  Results
  * are identical; only speed differs. */
 phos_status phos_validate_config(uint32_t variant);
+/* Grid of phos_validate: 0 (default) = one CTA per SM, else that many CTAs
+ * (at most 4096; each CTA stages the table once).  Process-wide. */
+phos_status phos_validate_grid(uint32_t ctas);
 
 /* --------------------------------------------------------- copy engine */
 
@@ -234,6 +237,16 @@ phos_status phos_copy_config(uint64_t tile_bytes, uint32_t ctas_per_sm);
  * align256(size) of the buffers before it; returns the total bytes. */
 uint64_t phos_image_bytes(const phos_table_t *t);
 phos_status phos_image_offsets(const phos_table_t *t, uint64_t *img_off_out);
+
+/* Checkpoint frequency for fault tolerance (Appendix A.1): N GPUs, each
+ * failing F times per hour, checkpoint overhead O hours, restore time R
+ * hours, job length T hours.  Wasted GPU hours at f checkpoints per hour:
+ *   W(f) = N F T (R + N / (2 f)) + N O f T
+ * (the paper's formula, taken as printed), minimised at f* = sqrt(N F / (2 O)).
+ * Writes f* and W(f*); EINVAL unless N, F, O > 0 and R, T >= 0. */
+phos_status phos_ckpt_frequency(double n_gpus, double fail_per_hour, double overhead_h,
+                                double restore_h, double hours, double *f_opt,
+                                double *wasted_at_opt);
 
 /* ---------------------------------------------------------- batched plan
  *

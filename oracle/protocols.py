@@ -361,3 +361,14 @@ def concurrent_restore(proc, image, kernels, chunk, quota):
         proc.run_kernel(j, kernels[j])
     return Result(ondemand=ondemand, copier_log=cp.log, misspec=misspec,
                   kernels_during=run_during, stats=stats)
+
+
+def wasted_gpu_hours(n, f_fail, overhead, restore, hours, f):
+    """Appendix A.1 cost, as printed: failures cost N F T (R + N / (2 f)),
+    checkpoints cost N O f T."""
+    return n * f_fail * hours * (restore + n / (2.0 * f)) + n * overhead * f * hours
+
+
+def optimal_frequency(n, f_fail, overhead):
+    """Appendix A.1: f* = sqrt(N F / (2 O))."""
+    return (n * f_fail / (2.0 * overhead)) ** 0.5

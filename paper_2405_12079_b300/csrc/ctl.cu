@@ -6,7 +6,10 @@
 // stream.  Copy lists are staged in a pinned host arena and uploaded with
 // one asynchronous copy per batch; the arena is recycled at the stream
 // synchronisations that after_kernel performs anyway to read the victims.
+#include <math.h>
 #include <string.h>
+
+#include <cmath>
 
 #include <algorithm>
 #include <vector>
@@ -282,6 +285,16 @@ phos_status copy_log(const std::vector<uint64_t> &log, uint64_t *out, uint64_t c
 }  // namespace phos
 
 using namespace phos;
+
+extern "C" phos_status phos_ckpt_frequency(double n, double f_fail, double o, double r,
+                                           double t, double *f_opt, double *wasted) {
+    if (!(n > 0) || !(f_fail > 0) || !(o > 0) || !(r >= 0) || !(t >= 0))
+        return fail(PHOS_EINVAL, "ckpt_frequency: need N, F, O > 0 and R, T >= 0");
+    const double fs = std::sqrt(n * f_fail / (2.0 * o));
+    if (f_opt) *f_opt = fs;
+    if (wasted) *wasted = n * f_fail * t * (r + n / (2.0 * fs)) + n * o * fs * t;
+    return PHOS_OK;
+}
 
 extern "C" phos_status phos_host_copy_config(uint64_t dma_min_bytes) {
     g_dma_min = dma_min_bytes;

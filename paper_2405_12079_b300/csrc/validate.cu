@@ -548,6 +548,7 @@ static size_t plan_batched(uint32_t n, int device, bool *smem_table) {
 }
 
 static uint32_t g_val_variant = 0;  // 0 auto, 1 TMA ring, 2 batched leaders
+static uint32_t g_val_ctas = 0;     // 0 auto (one per SM), else the grid size
 
 // Words per warp batch: 32 (most amortisation of the leader searches)
 // unless that leaves fewer than two batches per warp of the grid; then 16,
@@ -569,6 +570,12 @@ extern "C" phos_status phos_validate_config(uint32_t variant) {
     return PHOS_OK;
 }
 
+extern "C" phos_status phos_validate_grid(uint32_t ctas) {
+    if (ctas > 4096) return fail(PHOS_EINVAL, "validate_grid: %u CTAs", ctas);
+    g_val_ctas = ctas;
+    return PHOS_OK;
+}
+
 extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
                                      const uint64_t *d_trace, uint64_t n_rec,
                                      uint32_t access_bytes, uint32_t *d_bitmap,
@@ -587,7 +594,7 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     phos_table *T = const_cast<phos_table *>(t);
     const uint32_t variant = g_val_variant == 0 ? 2u : g_val_variant;
-    const int sms = sm_count(T->device);
+    const int sms = g_val_ctas ? (int)g_val_ctas : sm_count(T->device);
     const uint32_t wpb = words_per_batch(n_rec, (uint64_t)sms);
     const uint64_t unit = variant == 1 ? kTileRec : 32ull * wpb;
     const uint64_t units = (n_rec + unit - 1) / unit;

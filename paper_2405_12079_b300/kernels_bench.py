@@ -92,6 +92,12 @@ def bench_validate(K, out, variants=(1, 2)):
         ms = timeit(lambda: g.replay(), 3, 1) / K
         out["validate_per_trace_graph_" + tag] = dict(records=n1, us=1e3 * ms,
                                                       grec_s=n1 / ms / 1e6)
+    # grid sweep for one 1.3M-record trace (launch-bound shape)
+    for ctas in (148, 147, 128, 96, 74, 48, 37, 24):
+        phos.validate_grid(ctas)
+        ms = timeit(lambda: [run(big.data_ptr() + 8 * n1 * j, n1) for j in range(K)], 3, 1) / K
+        out["validate_per_trace_grid%d" % ctas] = dict(us=1e3 * ms)
+    phos.validate_grid(0)
     phos.validate_config(0)
 
 

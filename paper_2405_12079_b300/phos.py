@@ -48,7 +48,10 @@ _SIGS = {
     "phos_copy": (_i32, [_vp, _vp, _u32, _vp, _u64, _vp, _u64, _vp, _vp, _vp]),
     "phos_copy_config": (_i32, [_u64, _u32]),
     "phos_validate_config": (_i32, [_u32]),
+    "phos_validate_grid": (_i32, [_u32]),
     "phos_host_copy_config": (_i32, [_u64]),
+    "phos_ckpt_frequency": (_i32, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
+                                   _c.c_double, _P(_c.c_double), _P(_c.c_double)]),
     "phos_validate_noalloc": (_i32, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _u64,
                                       _vp, _vp]),
     "phos_image_bytes": (_u64, [_vp]),
@@ -276,6 +279,18 @@ def copy(table, d_list, n, d_staging=None, staging_bytes=0, image=None, image_by
 
 def validate_config(variant=0):
     return check(lib().phos_validate_config(variant), "validate_config")
+
+
+def ckpt_frequency(n_gpus, fail_per_hour, overhead_h, restore_h, hours):
+    """Appendix A.1: (f*, wasted GPU hours at f*)."""
+    f, w = _c.c_double(), _c.c_double()
+    check(lib().phos_ckpt_frequency(n_gpus, fail_per_hour, overhead_h, restore_h, hours,
+                                    _c.byref(f), _c.byref(w)), "ckpt_frequency")
+    return f.value, w.value
+
+
+def validate_grid(ctas=0):
+    return check(lib().phos_validate_grid(ctas), "validate_grid")
 
 
 def host_copy_config(dma_min_bytes=0):
