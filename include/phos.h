@@ -406,6 +406,7 @@ typedef struct {
                                 stop-the-world fallback, or -1               */
     uint32_t done;           /* 1 once the image is complete                 */
     uint32_t dirty;          /* recopy: size of the dirty set                */
+    uint64_t passes;         /* recopy: extra concurrent passes started      */
 } phos_ckpt_stats_t;
 
 /* Start a checkpoint at t1 (the caller has quiesced: Sec. 4.2 phase 1).
@@ -432,11 +433,21 @@ phos_status phos_ckpt_after_kernel(phos_ckpt_t *c, const uint64_t *d_trace, uint
 /* Drain the rest; recopy: quiesce point t2, recopy the dirty set whole.
  * Synchronises. */
 phos_status phos_ckpt_finish(phos_ckpt_t *c);
+/* Iterative recopy (Sec. 4.3 "iteratively do the concurrent recopy"): when
+ * a recopy session's copier has finished a pass (advance reported done),
+ * start another concurrent pass over the current dirty set instead of
+ * quiescing: those buffers become pending (copied from their start again)
+ * and the dirty set empties; the dirty rule is unchanged.  *pass_bytes =
+ * bytes of the new pass.  The caller decides when to stop (for instance
+ * when the dirty bytes stop shrinking) and then calls phos_ckpt_finish,
+ * which recopies the remaining dirty set stop-the-world. */
+phos_status phos_ckpt_begin_pass(phos_ckpt_t *c, uint64_t *pass_bytes);
 phos_status phos_ckpt_stats(const phos_ckpt_t *c, phos_ckpt_stats_t *out);
 /* Event logs, 5 u64 per event (n_out = number of events available):
  *   0 CoW:     round, buffer, 1 = staging / 2 = direct, offset, len
  *   1 copier:  round, buffer, offset in buffer, len, 1 if from a shadow
- *   2 dirty:   buffer, 0, 0, 0, 0 (ascending)                            */
+ *   2 dirty:   buffer, 0, 0, 0, 0 (ascending)
+ *   3 passes:  round, buffers, bytes, 0, 0 (one per phos_ckpt_begin_pass) */
 phos_status phos_ckpt_log(const phos_ckpt_t *c, uint32_t kind, uint64_t *out, uint64_t cap,
                           uint64_t *n_out);
 phos_status phos_ckpt_end(phos_ckpt_t *c);

@@ -304,6 +304,70 @@ def recopy_checkpoint(proc, kernels, chunk, quota):
                   stats=stats)
 
 
+def iterative_recopy(proc, kernels, chunk, quota, max_passes, stop_bytes):
+    """Iterative concurrent recopy (Section 4.3: "we can also iteratively do
+    the concurrent recopy", pre-copy in the style of live migration).
+
+    Pass 0 is the soft recopy's concurrent copy of every buffer.  Whenever
+    the copier finishes a pass, if fewer than ``max_passes`` extra passes
+    ran, the dirty bytes exceed ``stop_bytes`` and they shrank since the
+    previous pass, the dirty buffers become pending again and a new
+    concurrent pass recopies them while the kernels keep running (the same
+    dirty rule applies: written while in flight or after being copied);
+    otherwise the checkpoint quiesces (t2) and recopies the dirty set
+    stop-the-world.  The pass starts in the round whose copier move
+    finished the previous pass, before that round's kernel."""
+    n = proc.n
+    image = np.zeros(proc.image_bytes, np.uint8)
+    cp = Copier(n, proc.size, chunk)
+    dirty = set()
+    passes = []                           # (round, buffers, bytes) of each extra pass
+    stats = dict(copier_bytes=0, recopy_bytes=0)
+
+    def move(i, off, ln):
+        io = int(proc.img_off[i]) + off
+        image[io:io + ln] = proc.buf(i)[off:off + ln]
+        stats["copier_bytes"] += ln
+        return False
+
+    prev = None
+    k = 0
+    while k < len(kernels):
+        cp.advance(quota, move, k)
+        if cp.done():
+            db = sum(int(proc.size[i]) for i in dirty)
+            if len(passes) < max_passes and db > stop_bytes and (prev is None or db < prev):
+                for i in sorted(dirty):
+                    cp.state[i] = PENDING
+                    cp.copied[i] = 0
+                cp.cursor = 0
+                passes.append((k, sorted(dirty), db))
+                prev = db
+                dirty = set()
+            else:
+                break
+        kern = kernels[k]
+        perm = proc.speculate(kern)
+        touched = [cp.state[i] != PENDING for i in range(n)]
+        for i in np.nonzero(perm & PERM_W)[0]:
+            if touched[int(i)]:
+                dirty.add(int(i))
+        proc.run_kernel(k, kern)
+        res = proc.validate(perm, kern)
+        for v in victims_of_store(proc, perm, kern, res):
+            if touched[v]:
+                dirty.add(v)
+        k += 1
+    if not cp.done():
+        cp.advance(1 << 62, move, k)
+    for i in sorted(dirty):
+        sz, io = int(proc.size[i]), int(proc.img_off[i])
+        image[io:io + sz] = proc.buf(i)
+        stats["recopy_bytes"] += sz
+    return Result(image=image, dirty=sorted(dirty), passes=passes, copier_log=cp.log,
+                  kernels_run=k, stats=stats)
+
+
 def concurrent_restore(proc, image, kernels, chunk, quota):
     """Section 6 soft on-demand concurrent restore, then the rest of the
     kernels.  proc.mem holds whatever was there before (not restored)."""

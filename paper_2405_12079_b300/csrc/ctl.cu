@@ -314,6 +314,7 @@ struct phos_ckpt {
     std::vector<uint8_t> touched;  // recopy: in flight or done when the kernel ran
     std::vector<uint8_t> dirty;
     std::vector<uint64_t> cow_log;
+    std::vector<uint64_t> pass_log;
     uint64_t cow_bytes = 0, direct_bytes = 0, copier_bytes = 0, recopy_bytes = 0;
     int64_t misspec = -1;
     bool complete = false, finished = false, in_kernel = false;
@@ -529,6 +530,29 @@ extern "C" phos_status phos_ckpt_finish(phos_ckpt_t *c) {
     return S.sync();
 }
 
+extern "C" phos_status phos_ckpt_begin_pass(phos_ckpt_t *c, uint64_t *pass_bytes) {
+    if (!c) return fail(PHOS_EINVAL, "ckpt_begin_pass: NULL session");
+    if (c->mode != PHOS_CKPT_RECOPY) return fail(PHOS_EINVAL, "ckpt_begin_pass: recopy only");
+    if (c->in_kernel || c->finished)
+        return fail(PHOS_EINVAL, "ckpt_begin_pass: inside a kernel round or finished");
+    Session &S = c->ss;
+    if (!S.done()) return fail(PHOS_EINVAL, "ckpt_begin_pass: the current pass is not done");
+    uint64_t bytes = 0, nb = 0;
+    for (uint32_t i = 0; i < S.n; ++i) {
+        if (!c->dirty[i]) continue;
+        S.state[i] = kPending;
+        S.copied[i] = 0;
+        c->dirty[i] = 0;
+        bytes += S.t->size[i];
+        ++nb;
+    }
+    S.cursor = 0;
+    c->complete = S.done();
+    c->pass_log.insert(c->pass_log.end(), {S.round, nb, bytes, 0, 0});
+    if (pass_bytes) *pass_bytes = bytes;
+    return PHOS_OK;
+}
+
 extern "C" phos_status phos_ckpt_stats(const phos_ckpt_t *c, phos_ckpt_stats_t *o) {
     if (!c || !o) return fail(PHOS_EINVAL, "ckpt_stats: NULL argument");
     memset(o, 0, sizeof *o);
@@ -544,6 +568,7 @@ extern "C" phos_status phos_ckpt_stats(const phos_ckpt_t *c, phos_ckpt_stats_t *
     uint32_t nd = 0;
     for (uint8_t x : c->dirty) nd += x;
     o->dirty = nd;
+    o->passes = c->pass_log.size() / 5;
     return PHOS_OK;
 }
 
@@ -558,6 +583,7 @@ extern "C" phos_status phos_ckpt_log(const phos_ckpt_t *c, uint32_t kind, uint64
             if (c->dirty[i]) v.insert(v.end(), {i, 0, 0, 0, 0});
         return copy_log(v, out, cap, n_out);
     }
+    if (kind == 3) return copy_log(c->pass_log, out, cap, n_out);
     return fail(PHOS_EINVAL, "ckpt_log: kind %u", kind);
 }
 

@@ -75,6 +75,7 @@ _SIGS = {
     "phos_ckpt_before_kernel": (_i32, [_vp, _vp]),
     "phos_ckpt_after_kernel": (_i32, [_vp, _vp, _u64, _P(_c.c_int)]),
     "phos_ckpt_finish": (_i32, [_vp]),
+    "phos_ckpt_begin_pass": (_i32, [_vp, _P(_u64)]),
     "phos_ckpt_stats": (_i32, [_vp, _vp]),
     "phos_ckpt_log": (_i32, [_vp, _u32, _vp, _u64, _P(_u64)]),
     "phos_ckpt_end": (_i32, [_vp]),
@@ -126,7 +127,7 @@ class CkptStats(_c.Structure):
     _fields_ = [("kernels", _u64), ("copier_bytes", _u64), ("cow_bytes", _u64),
                 ("direct_bytes", _u64), ("recopy_bytes", _u64), ("validated", _u64),
                 ("violations", _u64), ("misspec_round", _c.c_int64), ("done", _u32),
-                ("dirty", _u32)]
+                ("dirty", _u32), ("passes", _u64)]
 
 
 class RestoreDesc(_c.Structure):
@@ -358,6 +359,11 @@ class Checkpoint:
 
     def finish(self):
         check(lib().phos_ckpt_finish(self.h), "ckpt_finish")
+
+    def begin_pass(self):
+        b = _u64()
+        check(lib().phos_ckpt_begin_pass(self.h, _c.byref(b)), "ckpt_begin_pass")
+        return int(b.value)
 
     def stats(self):
         st = CkptStats()

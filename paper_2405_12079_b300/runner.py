@@ -75,18 +75,29 @@ class DeviceProcess:
     def run_cow(self, image, quota, chunk, staging=None, staging_bytes=0):
         return self._ckpt(phos.CKPT_COW, image, quota, chunk, staging, staging_bytes)
 
-    def run_recopy(self, image, quota, chunk):
-        return self._ckpt(phos.CKPT_RECOPY, image, quota, chunk, None, 0)
+    def run_recopy(self, image, quota, chunk, max_passes=0, stop_bytes=0):
+        """Soft recopy; with max_passes > 0, iterative: each time the copier
+        finishes a pass, another concurrent pass recopies the dirty set while
+        its bytes exceed stop_bytes and keep shrinking."""
+        return self._ckpt(phos.CKPT_RECOPY, image, quota, chunk, None, 0, max_passes,
+                          stop_bytes)
 
-    def _ckpt(self, mode, image, quota, chunk, staging, staging_bytes):
+    def _ckpt(self, mode, image, quota, chunk, staging, staging_bytes, max_passes=0,
+              stop_bytes=0):
         s = self.stream()
         c = phos.Checkpoint(self.table, mode, image.data_ptr(), image.numel(), chunk, 4,
                             staging.data_ptr() if staging is not None else None, staging_bytes, s)
         k, misspec = 0, False
         K = len(self.kernels)
+        prev, passes = None, 0
         while k < K:
             if c.advance(quota):
-                break
+                db = self.dirty_bytes(c) if max_passes else 0
+                if passes < max_passes and db > stop_bytes and (prev is None or db < prev):
+                    c.begin_pass()
+                    prev, passes = db, passes + 1
+                else:
+                    break
             pk = self.kernels[k]
             c.before_kernel(pk.speculate(self.table, self.perm))
             self.run_kernel(k)
@@ -96,9 +107,13 @@ class DeviceProcess:
                 break
         c.finish()
         out = dict(stats=c.stats(), cow=c.log(0), copier=c.log(1), dirty=c.log(2)[:, 0],
-                   kernels_run=k)
+                   passes=c.log(3), kernels_run=k)
         c.close()
         return out
+
+    def dirty_bytes(self, c):
+        d = c.log(2)[:, 0].astype(np.int64)
+        return int(self.layout.size[d].sum()) if len(d) else 0
 
     def run_restore(self, image, quota, chunk, d_present=None):
         """Concurrent restore followed by the rest of the kernels."""

@@ -29,6 +29,7 @@ def test_training_line_contract():
     assert line["value"] > 0 and line["gpu_launches"] > 0
     assert line["verified"]["cow_image_equals_memory_at_t1"]
     assert line["verified"]["recopy_image_equals_memory_at_t2"]
+    assert line["verified"]["iterative_recopy_image_equals_memory_at_t2"]
     r = line["roofline"]
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert k in r

@@ -183,3 +183,33 @@ def test_restore_stray_load_rolls_back():
     w = World(cfg["layout"], cfg["seed"], mk)
     got, exp = check_restore(w, a256(w.dp.image_bytes / 80), 32 * 1024)
     assert exp.misspec is not None
+
+
+@pytest.mark.parametrize("div,n_kernels,stray,max_passes,stop", [
+    (100, 200, 0.0, 6, 0), (30, 200, 0.0, 6, 0), (30, 200, 0.0, 1, 0),
+    (20, 120, 0.3, 6, 1 << 20)])
+def test_iterative_recopy(div, n_kernels, stray, max_passes, stop):
+    """Iterative concurrent recopy (Sec. 4.3): the passes (round, buffers,
+    bytes), the copier pieces across passes, the final dirty set, the image
+    at t2 and live memory all equal the oracle's; the stop-the-world recopy
+    shrinks against the single-pass protocol on the same workload."""
+    w, cfg = training_world(wl.SEED0 + 2, 0.002 if n_kernels == 200 else 0.001, n_kernels,
+                            stray_store_frac=stray)
+    quota = a256(w.dp.image_bytes / div)
+    chunk = 64 * 1024
+    img = torch.zeros(w.dp.image_bytes, dtype=torch.uint8).pin_memory()
+    proc = w.oracle_proc()
+    exp = P.iterative_recopy(proc, w.kernels, chunk, quota, max_passes, stop)
+    got = w.dp.run_recopy(img, quota, chunk, max_passes=max_passes, stop_bytes=stop)
+    torch.cuda.synchronize()
+    assert len(exp.passes) >= 1
+    assert [(int(r), int(nb), int(b)) for r, nb, b, _, _ in got["passes"]] == \
+        [(k, len(bs), b) for k, bs, b in exp.passes]
+    assert got["stats"]["passes"] == len(exp.passes)
+    assert got["kernels_run"] == exp.kernels_run
+    assert [tuple(int(x) for x in r) for r in got["copier"]] == copier_rows(exp.copier_log)
+    assert got["dirty"].tolist() == exp.dirty
+    assert got["stats"]["recopy_bytes"] == exp.stats["recopy_bytes"]
+    assert got["stats"]["copier_bytes"] == exp.stats["copier_bytes"]
+    assert np.array_equal(img.numpy(), exp.image)
+    assert w.live_equal(proc)

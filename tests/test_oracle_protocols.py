@@ -234,3 +234,33 @@ def test_first_fit_allocator():
     a.release(256, 512)
     a.release(0, 256)
     assert a.free == [(0, 1024)]
+
+
+@pytest.mark.parametrize("seed,passes", [(80, 3), (81, 6)])
+def test_iterative_recopy_image_equals_memory_at_t2(seed, passes):
+    """Iterative concurrent recopy: the image still equals memory at t2, and
+    the stop-the-world recopy at the end is no larger than the single-round
+    protocol's (each extra pass only starts when the dirty bytes shrink)."""
+    rng, lay, proc = make_proc(seed, n=40)
+    ks = seq(rng, lay, 200)
+    mem0 = proc.mem.copy()
+    one = P.recopy_checkpoint(proc, ks, 4096, 16384)
+    proc.mem[:] = mem0
+    res = P.iterative_recopy(proc, ks, 4096, 16384, passes, 0)
+    assert np.array_equal(res.image, P.stw_checkpoint(proc))
+    assert len(res.passes) >= 1
+    sizes = [b for _, _, b in res.passes]
+    assert all(x > y for x, y in zip(sizes, sizes[1:]))     # strictly shrinking
+    assert res.stats["recopy_bytes"] <= one.stats["recopy_bytes"] or \
+        res.kernels_run > one.kernels_run
+
+
+def test_iterative_recopy_without_extra_passes_is_the_soft_recopy():
+    rng, lay, proc = make_proc(82, n=30)
+    ks = seq(rng, lay, 80)
+    mem0 = proc.mem.copy()
+    one = P.recopy_checkpoint(proc, ks, 4096, 8192)
+    proc.mem[:] = mem0
+    it = P.iterative_recopy(proc, ks, 4096, 8192, 0, 0)
+    assert it.dirty == one.dirty and it.copier_log == one.copier_log
+    assert it.kernels_run == one.kernels_run and np.array_equal(it.image, one.image)
