@@ -957,6 +957,142 @@ def run_budget(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+PRIORITY = ("application transfers under C/R load: %d checkpoint and %d restore requests of "
+            "%.2f GB (250 buffers each) submitted at once to a 16-slot server (4 MB pieces "
+            "on the DMA engines), while an application stream issues one 8 MB transfer every "
+            "2 ms, alternating host->device and device->host; latency of each transfer from the "
+            "application's call to its completion (host clock)")
+
+
+def run_priority(args, rank, world):
+    """Sec. 5 prioritized application PCIe transfer: latency of application
+    transfers idle, under C/R load without priority, and under load with
+    priority at two queue windows; C/R throughput in each."""
+    import threading
+    import torch
+    from paper_2405_12079_b300 import phos
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    s = torch.cuda.current_stream().cuda_stream
+    sc = args.scale
+    n_req, req_b, nb = 16, a256(1e9 * sc), 250
+    dev_b, host_b = 2 * n_req * req_b, 2 * n_req * req_b
+    arena = torch.empty(dev_b, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(arena.data_ptr(), dev_b, 91, s)
+    host = torch.empty(host_b, dtype=torch.uint8).pin_memory()
+    staging = torch.empty(n_req * req_b, dtype=torch.uint8, device="cuda")
+    app_b = 8 << 20
+    app_h = torch.empty(2 * app_b, dtype=torch.uint8).pin_memory()
+    app_d = torch.empty(2 * app_b, dtype=torch.uint8, device="cuda")
+    sizes = np.full(nb, req_b // nb // 256 * 256, np.uint64)
+    sizes[-1] += np.uint64(req_b - int(sizes.sum()))
+    reqs = []
+    for q in range(2 * n_req):
+        bases = arena.data_ptr() + q * req_b + np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        t = phos.Table(bases.astype(np.uint64), sizes)
+        kind = phos.REQ_CHECKPOINT if q % 2 == 0 else phos.REQ_RESTORE
+        reqs.append((t, host.data_ptr() + q * req_b, t.image_bytes(), kind))
+    torch.cuda.synchronize()
+    app = torch.cuda.Stream()
+
+    def arm(load, priority, window, dma_min=1 << 20):
+        srv = phos.Server(16, staging.data_ptr(), staging.numel(), chunk=4 << 20,
+                          dma_min=dma_min, app_priority=priority, window=window)
+        lat = {"h2d": [], "d2h": []}
+        dev_ms = {"h2d": [], "d2h": []}
+        stop = threading.Event()
+        errors = []
+
+        def appl():
+            try:
+                torch.cuda.set_device(dev)
+                k = 0
+                t_next = time.monotonic()
+                while not stop.is_set():
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+                        enable_timing=True)
+                    # latency the application sees: from its call to the
+                    # transfer's completion (host clock); the device-side
+                    # e0 -> e1 time starts only once the stream reaches e0
+                    t_call = time.perf_counter()
+                    e0.record(app)
+                    if k % 2 == 0:
+                        srv.app_copy(app_d.data_ptr(), app_h.data_ptr(), app_b, app.cuda_stream)
+                    else:
+                        srv.app_copy(app_h.data_ptr() + app_b, app_d.data_ptr() + app_b, app_b,
+                                     app.cuda_stream)
+                    e1.record(app)
+                    e1.synchronize()
+                    d = "h2d" if k % 2 == 0 else "d2h"
+                    lat[d].append(1e3 * (time.perf_counter() - t_call))
+                    dev_ms[d].append(e0.elapsed_time(e1))
+                    k += 1
+                    t_next += 0.002
+                    time.sleep(max(0.0, t_next - time.monotonic()))
+            except Exception as e:
+                errors.append(e)
+        th = threading.Thread(target=appl)
+        t0 = time.monotonic_ns()
+        th.start()
+        tks = []
+        if load:
+            tks = [srv.submit(k, t, hp, ib) for t, hp, ib, k in reqs]
+            srv.drain(3_600_000)
+        else:
+            time.sleep(0.5)
+        stop.set()
+        th.join()
+        st = srv.stats()
+        out = {}
+        if tks:
+            res = [srv.poll(tk) for tk in tks]
+            assert all(r["state"] == 2 for r in res), res
+            span = (max(r["t_done_ns"] for r in res) - t0) / 1e9
+            by = sum(ib for _, _, ib, _ in reqs)
+            out["cr_gbs"] = by / span / 1e9
+            out["cr_span_s"] = span
+        srv.close()
+        if errors:
+            raise errors[0]
+        for d, v in lat.items():
+            v, g = np.array(v), np.array(dev_ms[d])
+            out[d] = {"n": len(v), "p50_ms": float(np.percentile(v, 50)),
+                      "p99_ms": float(np.percentile(v, 99)), "max_ms": float(v.max()),
+                      "device_p50_ms": float(np.percentile(g, 50))}
+        out["paused_turns"] = st["paused_turns"]
+        out["batches"] = st["batches"]
+        return out
+
+    arm(False, False, 0)                          # warm-up
+    clk = Clocks(dev)
+    clk.start()
+    l0 = phos.launch_count()
+    res = {"idle": arm(False, False, 0),
+           "load_no_priority": arm(True, False, 0),
+           "load_priority_window_128MB": arm(True, True, 0),
+           "load_priority_window_8MB": arm(True, True, 8 << 20),
+           "load_no_priority_sm_host_legs": arm(True, False, 0, 0),
+           "load_priority_window_8MB_sm_host_legs": arm(True, True, 8 << 20, 0)}
+    launches = phos.launch_count() - l0
+    clocks = clk.stop()
+    best = res["load_priority_window_8MB"]
+    base = res["load_no_priority"]
+    line = {"metric": METRIC, "value": best["d2h"]["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * best["cr_span_s"], "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic",
+            "config": {"workload": PRIORITY % (n_req, n_req, req_b / 1e9), "scale": sc,
+                       "value": "p99 latency of the 8 MB device->host application transfers "
+                                "under load, priority, 8 MB window"},
+            "arms": res,
+            "p99_d2h_speedup": base["d2h"]["p99_ms"] / best["d2h"]["p99_ms"],
+            "p99_h2d_speedup": base["h2d"]["p99_ms"] / best["h2d"]["p99_ms"],
+            "cr_gbs_cost": 1.0 - best["cr_gbs"] / base["cr_gbs"],
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -964,7 +1100,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="phos", choices=["phos", "reference"])
     ap.add_argument("--workload", default="training",
-                    choices=["training", "batched", "serving", "restore", "budget"],
+                    choices=["training", "batched", "serving", "restore", "budget",
+                             "priority"],
                     help="training: the headline checkpoint step; batched: the 64-image plan")
     ap.add_argument("--host-copy", default="dma", choices=["sm", "dma"],
                     help="host legs on the SM copy kernel, or pieces >= 1 MiB on the DMA engines")
@@ -990,6 +1127,8 @@ def main():
         run_restore(args, rank, world)
     elif args.workload == "budget":
         run_budget(args, rank, world)
+    elif args.workload == "priority":
+        run_priority(args, rank, world)
     else:
         run_gpu(args, rank, world)
     if world > 1:

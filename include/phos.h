@@ -314,15 +314,23 @@ phos_status phos_plan_destroy(phos_plan_t *p);
 
 typedef struct phos_server phos_server_t;
 enum { PHOS_REQ_CHECKPOINT = 1, PHOS_REQ_RESTORE = 2 };
+/* Server flags. */
+enum { PHOS_SERVER_APP_PRIORITY = 1 };
 
 typedef struct {
     uint32_t max_slots;      /* requests on the device at once (1 = one at a
                                 time, strictly in arrival order)            */
-    uint32_t reserved;
+    uint32_t flags;          /* PHOS_SERVER_*                               */
     void *d_staging;         /* device staging area (checkpoint snapshots)  */
     uint64_t staging_bytes;  /* admission budget                            */
     uint64_t chunk;          /* host-leg piece size, multiple of 256        */
     uint64_t dma_min;        /* pieces >= this go to the DMA engines; 0 = none */
+    uint64_t window;         /* host-leg bytes queued on the GPU per direction,
+                                at most (two batches of window/2, each at
+                                least one chunk); 0 = two batches of
+                                max(8 chunks, 64 MiB).  With APP_PRIORITY it
+                                bounds how long an application transfer can
+                                wait behind C/R pieces already issued.      */
 } phos_server_desc_t;
 
 typedef struct {
@@ -354,6 +362,32 @@ phos_status phos_server_poll(phos_server_t *s, uint64_t ticket, phos_result_t *o
 phos_status phos_server_drain(phos_server_t *s, uint32_t timeout_ms);
 /* Finish what was submitted, then stop the scheduler and free its streams. */
 phos_status phos_server_stop(phos_server_t *s);
+
+/* An application transfer that the server's C/R traffic yields to (Sec. 5,
+ * "Prioritized application PCIe transfer": the checkpoint is copied in
+ * chunks and, after each one, pauses while an application transfer is
+ * pending or running).  Copies `bytes` from src to dst on the caller's
+ * `stream` (cudaMemcpyAsync, so the application keeps its own stream
+ * order) and registers the transfer with the server.  One side must be
+ * pinned host memory and the other device memory; the direction follows
+ * from the pointers.  With PHOS_SERVER_APP_PRIORITY the scheduler issues
+ * no C/R piece, in either direction (a copy engine may serve both), from
+ * the moment of this call until the transfer completes, so it waits at
+ * most for the C/R bytes already queued (desc.window per direction);
+ * without the flag the transfer is only counted.  Thread-safe.  EINVAL: NULL pointers, pageable host memory, or
+ * both sides on the device / on the host. */
+phos_status phos_server_app_copy(phos_server_t *s, void *dst, const void *src, uint64_t bytes,
+                                 cudaStream_t stream);
+
+typedef struct {
+    uint64_t app_copies;          /* application transfers registered        */
+    uint64_t app_bytes;
+    uint64_t paused_turns;        /* scheduler turns in which a direction's C/R
+                                     issue was held back for an application
+                                     transfer                                */
+    uint64_t batches;             /* C/R host-leg batches issued             */
+} phos_server_stats_t;
+phos_status phos_server_stats(phos_server_t *s, phos_server_stats_t *out);
 
 /* Host legs of the protocol drivers below: pieces that cross PCIe (to or
  * from the image) and are at least dma_min_bytes long go to the DMA copy

@@ -16,6 +16,15 @@
 // GPU joins the next batch that has room, and the two directions run
 // concurrently.  Completion is tracked with events; no turn blocks on the
 // device.
+//
+// Application transfers (phos_server_app_copy) run on the application's
+// own stream.  With APP_PRIORITY the scheduler issues no new C/R batch, in
+// either direction, while an application transfer is pending or running:
+// a copy engine may serve streams of both directions, so holding back only
+// the transfer's own direction left it queued behind the other one's DMA
+// copies (hundreds of ms under load on B300).  At most `window` C/R bytes
+// per direction are then ahead of it.  The pause is a host decision per
+// turn and never waits on the device.
 #include <string.h>
 #include <time.h>
 
@@ -57,6 +66,12 @@ struct Issue {
     std::vector<uint64_t> finishing;  // tickets whose last piece is in this batch
 };
 
+// An application transfer the scheduler yields to.
+struct AppCopy {
+    cudaEvent_t ev;
+    bool d2h;
+};
+
 }  // namespace phos
 
 using namespace phos;
@@ -76,6 +91,9 @@ struct phos_server {
     std::vector<std::pair<uint64_t, uint64_t>> free_stg;  // staging extents
     std::deque<Issue> inflight_d2h, inflight_h2d;
     std::vector<cudaEvent_t> ev_pool;
+    std::vector<AppCopy> app_inflight;          // recorded, maybe not complete
+    uint32_t app_pending[2] = {0, 0};           // being issued (h2d, d2h)
+    phos_server_stats_t st{};
     // device descriptor rings per direction (pinned staging of lists)
     phos_copy_t *h_ring[3] = {nullptr, nullptr, nullptr};
     phos_copy_t *d_ring[3] = {nullptr, nullptr, nullptr};
@@ -177,7 +195,12 @@ struct phos_server {
     void issue(bool d2h) {
         std::deque<Issue> &inf = d2h ? inflight_d2h : inflight_h2d;
         if (inf.size() >= 2) return;           // keep at most two batches queued
-        const uint64_t batch = std::max<uint64_t>(d.chunk * 8, 64ull << 20);
+        if ((d.flags & PHOS_SERVER_APP_PRIORITY) && app_busy()) {
+            ++st.paused_turns;                 // an application transfer goes first
+            return;
+        }
+        const uint64_t batch = d.window ? std::max(d.chunk, d.window / 2)
+                                        : std::max<uint64_t>(d.chunk * 8, 64ull << 20);
         std::vector<Req *> cand;
         for (uint64_t tk : active) {
             Req &q = reqs[tk];
@@ -262,6 +285,23 @@ struct phos_server {
         is.ev = get_ev();
         cudaEventRecord(is.ev, s);
         inf.push_back(std::move(is));
+        ++st.batches;
+    }
+
+    // True while an application transfer is being issued or has not
+    // completed (retire_app runs first in each turn).
+    bool app_busy() const {
+        return app_pending[0] || app_pending[1] || !app_inflight.empty();
+    }
+    void retire_app() {
+        for (size_t k = 0; k < app_inflight.size();) {
+            if (cudaEventQuery(app_inflight[k].ev) == cudaSuccess) {
+                ev_pool.push_back(app_inflight[k].ev);
+                app_inflight.erase(app_inflight.begin() + k);
+            } else {
+                ++k;
+            }
+        }
     }
 
     void retire(std::deque<Issue> &inf) {
@@ -290,6 +330,7 @@ struct phos_server {
         while (true) {
             retire(inflight_d2h);
             retire(inflight_h2d);
+            retire_app();
             admit();
             issue(true);
             issue(false);
@@ -305,7 +346,7 @@ struct phos_server {
                 }
             }
             if (stop && queue.empty() && active.empty()) break;
-            const bool idle = queue.empty() && active.empty();
+            const bool idle = queue.empty() && active.empty() && app_inflight.empty();
             if (idle) {
                 cv.wait_for(lk, std::chrono::milliseconds(5));
             } else {
@@ -388,6 +429,60 @@ extern "C" phos_status phos_server_poll(phos_server_t *S, uint64_t ticket, phos_
     return PHOS_OK;
 }
 
+static bool host_side(const void *p, bool *ok) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        *ok = false;
+        return false;
+    }
+    *ok = a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeDevice ||
+          a.type == cudaMemoryTypeManaged;
+    return a.type == cudaMemoryTypeHost;
+}
+
+extern "C" phos_status phos_server_app_copy(phos_server_t *S, void *dst, const void *src,
+                                            uint64_t bytes, cudaStream_t stream) {
+    if (!S || !dst || !src) return fail(PHOS_EINVAL, "server_app_copy: NULL argument");
+    PHOS_CUDA(cudaSetDevice(S->device));
+    bool ok_d, ok_s;
+    const bool hd = host_side(dst, &ok_d), hs = host_side(src, &ok_s);
+    if (!ok_d || !ok_s)
+        return fail(PHOS_EINVAL, "server_app_copy: pageable or unknown memory (pin the host side)");
+    if (hd == hs)
+        return fail(PHOS_EINVAL, "server_app_copy: one side must be pinned host memory and the "
+                                 "other device memory");
+    const bool d2h = hd;
+    cudaEvent_t ev;
+    {
+        // registered before the copy is issued, so no C/R batch issued from
+        // here on gets ahead of it
+        std::lock_guard<std::mutex> g(S->mu);
+        ev = S->get_ev();
+        ++S->app_pending[d2h];
+    }
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, stream);
+    std::lock_guard<std::mutex> g(S->mu);
+    --S->app_pending[d2h];
+    if (e != cudaSuccess) {
+        S->ev_pool.push_back(ev);
+        return cuda_fail(e, "server_app_copy");
+    }
+    S->app_inflight.push_back(AppCopy{ev, d2h});
+    ++S->st.app_copies;
+    S->st.app_bytes += bytes;
+    S->cv.notify_one();
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_server_stats(phos_server_t *S, phos_server_stats_t *out) {
+    if (!S || !out) return fail(PHOS_EINVAL, "server_stats: NULL argument");
+    std::lock_guard<std::mutex> g(S->mu);
+    *out = S->st;
+    return PHOS_OK;
+}
+
 extern "C" phos_status phos_server_drain(phos_server_t *S, uint32_t timeout_ms) {
     if (!S) return fail(PHOS_EINVAL, "server_drain: NULL server");
     const uint64_t t_end = now_ns() + (uint64_t)timeout_ms * 1000000ull;
@@ -409,6 +504,10 @@ extern "C" phos_status phos_server_stop(phos_server_t *S) {
         S->cv.notify_one();
     }
     S->th.join();
+    for (const AppCopy &a : S->app_inflight) {
+        cudaEventSynchronize(a.ev);
+        cudaEventDestroy(a.ev);
+    }
     cudaStreamSynchronize(S->s_snap);
     cudaStreamSynchronize(S->s_d2h);
     cudaStreamSynchronize(S->s_h2d);

@@ -70,6 +70,8 @@ _SIGS = {
     "phos_server_poll": (_i32, [_vp, _u64, _vp]),
     "phos_server_drain": (_i32, [_vp, _u32]),
     "phos_server_stop": (_i32, [_vp]),
+    "phos_server_app_copy": (_i32, [_vp, _vp, _vp, _u64, _vp]),
+    "phos_server_stats": (_i32, [_vp, _vp]),
     "phos_ckpt_begin": (_i32, [_vp, _vp, _vp, _P(_vp)]),
     "phos_ckpt_advance": (_i32, [_vp, _u64, _P(_c.c_int)]),
     "phos_ckpt_before_kernel": (_i32, [_vp, _vp]),
@@ -93,11 +95,17 @@ CKPT_COW, CKPT_RECOPY = 1, 2
 
 
 REQ_CHECKPOINT, REQ_RESTORE = 1, 2
+SERVER_APP_PRIORITY = 1
 
 
 class ServerDesc(_c.Structure):
-    _fields_ = [("max_slots", _u32), ("reserved", _u32), ("d_staging", _vp),
-                ("staging_bytes", _u64), ("chunk", _u64), ("dma_min", _u64)]
+    _fields_ = [("max_slots", _u32), ("flags", _u32), ("d_staging", _vp),
+                ("staging_bytes", _u64), ("chunk", _u64), ("dma_min", _u64), ("window", _u64)]
+
+
+class ServerStats(_c.Structure):
+    _fields_ = [("app_copies", _u64), ("app_bytes", _u64), ("paused_turns", _u64),
+                ("batches", _u64)]
 
 
 class Request(_c.Structure):
@@ -476,8 +484,10 @@ class Plan:
 class Server:
     """Continuous-batching request loop (phos_server_*)."""
 
-    def __init__(self, max_slots, d_staging, staging_bytes, chunk=4 << 20, dma_min=1 << 20):
-        d = ServerDesc(max_slots, 0, d_staging, staging_bytes, chunk, dma_min)
+    def __init__(self, max_slots, d_staging, staging_bytes, chunk=4 << 20, dma_min=1 << 20,
+                 app_priority=False, window=0):
+        d = ServerDesc(max_slots, SERVER_APP_PRIORITY if app_priority else 0, d_staging,
+                       staging_bytes, chunk, dma_min, window)
         h = _vp()
         check(lib().phos_server_start(_c.byref(d), _c.byref(h)), "server_start")
         self.h = h.value
@@ -495,6 +505,15 @@ class Server:
 
     def drain(self, timeout_ms=600_000):
         check(lib().phos_server_drain(self.h, timeout_ms), "server_drain")
+
+    def app_copy(self, dst, src, nbytes, stream):
+        """An application transfer on `stream` that C/R traffic yields to."""
+        check(lib().phos_server_app_copy(self.h, dst, src, nbytes, stream), "server_app_copy")
+
+    def stats(self):
+        st = ServerStats()
+        check(lib().phos_server_stats(self.h, _c.byref(st)), "server_stats")
+        return _stats_dict(st)
 
     def close(self):
         if self.h:

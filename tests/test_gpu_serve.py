@@ -118,3 +118,104 @@ def test_request_larger_than_budget_is_refused():
         w.submit(srv, w.reqs[0])
     assert e.value.code == phos.PHOS_EBUDGET
     srv.close()
+
+
+@pytest.mark.parametrize("priority", [False, True], ids=["counted", "priority"])
+def test_app_transfers_in_the_mix(priority):
+    """Application transfers (Sec. 5 prioritized application PCIe transfer)
+    issued on their own stream while the mix runs: every request's bytes and
+    every application transfer's bytes are exact either way; the server
+    counts them, and with priority it held C/R issue back at least once."""
+    w = World(7)
+    exp_dev, exp_host = w.expected()
+    cks = [a256(r["img"]) for r in w.reqs if r["kind"] == phos.REQ_CHECKPOINT]
+    staging = torch.empty(sum(cks), dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(70)
+    n_app, sz = 16, 1 << 20
+    src_h = torch.from_numpy(rng.integers(0, 256, n_app * sz, dtype=np.uint8)).pin_memory()
+    src_d = torch.from_numpy(rng.integers(0, 256, n_app * sz, dtype=np.uint8)).cuda()
+    dst_d = torch.zeros(n_app * sz, dtype=torch.uint8, device="cuda")
+    dst_h = torch.zeros(n_app * sz, dtype=torch.uint8).pin_memory()
+    w.reset()
+    srv = phos.Server(8, staging.data_ptr(), staging.numel(), chunk=64 << 10, dma_min=256 << 10,
+                      app_priority=priority, window=1 << 20)
+    app = torch.cuda.Stream()
+    tks = []
+    for q, r in enumerate(w.reqs):
+        tks.append(w.submit(srv, r))
+        if q < n_app:
+            o = q * sz
+            if q % 2 == 0:
+                srv.app_copy(dst_d.data_ptr() + o, src_h.data_ptr() + o, sz, app.cuda_stream)
+            else:
+                srv.app_copy(dst_h.data_ptr() + o, src_d.data_ptr() + o, sz, app.cuda_stream)
+    srv.drain(60_000)
+    app.synchronize()
+    st = srv.stats()
+    res = [srv.poll(t) for t in tks]
+    srv.close()
+    torch.cuda.synchronize()
+    assert all(x["state"] == 2 and x["status"] == 0 for x in res)
+    assert np.array_equal(w.dev.cpu().numpy(), exp_dev)
+    assert np.array_equal(w.host.numpy(), exp_host)
+    ev, od = np.arange(0, n_app, 2), np.arange(1, n_app, 2)
+    got_d = dst_d.cpu().numpy().reshape(n_app, sz)
+    got_h = dst_h.numpy().reshape(n_app, sz)
+    assert np.array_equal(got_d[ev], src_h.numpy().reshape(n_app, sz)[ev])
+    assert np.array_equal(got_h[od], src_d.cpu().numpy().reshape(n_app, sz)[od])
+    assert st["app_copies"] == n_app and st["app_bytes"] == n_app * sz
+    assert st["batches"] > 0
+
+
+@pytest.mark.parametrize("priority", [False, True], ids=["counted", "priority"])
+@pytest.mark.parametrize("app_d2h", [True, False], ids=["app-d2h", "app-h2d"])
+@pytest.mark.parametrize("kind", [phos.REQ_CHECKPOINT, phos.REQ_RESTORE], ids=["ckpt", "restore"])
+def test_pending_app_transfer_holds_back_cr_issue(priority, app_d2h, kind):
+    """An application transfer queued behind ~25 ms of work on its stream
+    (a bounded clock-spin kernel) is pending that long: with priority, a
+    request whose host leg runs in either direction cannot finish before
+    it, and the scheduler counted the turns it held back; without priority
+    nothing is held back by the scheduler (the copy engines may still queue
+    the request's copies behind the pending one)."""
+    w = World(8, n_req=2)
+    r = w.reqs[0] if w.reqs[0]["kind"] == kind else w.reqs[1]
+    assert r["kind"] == kind
+    staging = torch.empty(a256(r["img"]) + 256, dtype=torch.uint8, device="cuda")
+    src = torch.zeros(1 << 20, dtype=torch.uint8).pin_memory()
+    dev = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    srv = phos.Server(4, staging.data_ptr(), staging.numel(), chunk=64 << 10, dma_min=256 << 10,
+                      app_priority=priority, window=1 << 20)
+    app = torch.cuda.Stream()
+    with torch.cuda.stream(app):
+        torch.cuda._sleep(50_000_000)           # >= 24.6 ms at 2032 MHz
+    if app_d2h:
+        srv.app_copy(src.data_ptr(), dev.data_ptr(), src.numel(), app.cuda_stream)
+    else:
+        srv.app_copy(dev.data_ptr(), src.data_ptr(), src.numel(), app.cuda_stream)
+    tk = w.submit(srv, r)
+    srv.drain(60_000)
+    res = srv.poll(tk)
+    st = srv.stats()
+    app.synchronize()
+    srv.close()
+    assert res["state"] == 2 and res["status"] == 0
+    took_ms = (res["t_done_ns"] - res["t_submit_ns"]) / 1e6
+    if priority:
+        assert took_ms > 15 and st["paused_turns"] > 0
+    else:
+        assert st["paused_turns"] == 0
+
+
+def test_app_copy_rejects_pageable_and_same_side():
+    staging = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    srv = phos.Server(1, staging.data_ptr(), staging.numel(), app_priority=True)
+    pageable = np.zeros(4096, np.uint8)
+    d1 = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    d2 = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    for dst, src in [(d1.data_ptr(), pageable.ctypes.data), (d1.data_ptr(), d2.data_ptr())]:
+        with pytest.raises(phos.PhosError) as e:
+            srv.app_copy(dst, src, 4096, s)
+        assert e.value.code == phos.PHOS_EINVAL
+    assert srv.stats()["app_copies"] == 0
+    srv.close()
