@@ -6,10 +6,13 @@ application kernels (each writes 1-20 random buffers and reads 1-20, with
 a 1.3M-record warp-coalesced access trace of 32 x 4-byte runs, 0.1 %
 stray loads).  One step is one soft copy-on-write checkpoint (Sec. 4.2,
 2 GB device staging) followed by one soft recopy checkpoint (Sec. 4.3),
-each taken in lockstep with the application: the background copier moves
-image/100 bytes per round in 4 MB pieces into a pinned host image; before
-each kernel its launch arguments are speculated, CoW copies or dirty
-marking happen, the kernel runs, and its trace is validated.
+each taken concurrently with the application: per kernel round the
+background copier is given image/100 bytes in 4 MB pieces for a pinned host
+image, which it copies on a stream of its own; before each kernel its
+launch arguments are speculated, CoW copies or dirty marking happen, the
+kernel runs, and its trace is validated, with the protocol's response to
+the validation applied on the device (``--rounds sync`` instead runs every
+round in lockstep on one stream and waits for each validation).
 
 Prints one JSON line.  ``value`` = bytes moved by the copy engine (CoW
 copies, background copy, direct copies, recopy) per second of step time.
@@ -31,8 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "validated accesses/s and C/R copy GB/s vs HBM/PCIe peak; request p50/p99"
 WORKLOAD = ("training-process image: 1,000 buffers, log-normal 256 B-512 MB, 40 GB; "
             "200-kernel mutator sequence writing 1-20 buffers each; 1.3M-record coalesced "
-            "trace per kernel (0.1% stray); soft CoW then soft recopy, lockstep, "
-            "quota image/100, 4 MB pieces, 2 GB staging, pinned host image")
+            "trace per kernel (0.1% stray); soft CoW then soft recopy, copier quota "
+            "image/100 per kernel round, 4 MB pieces, 2 GB staging, pinned host image")
 
 
 def a256(x):
@@ -220,10 +223,12 @@ def run_gpu(args, rank, world):
         # lockstep round with phase marks (same calls as runner.DeviceProcess);
         # max_passes > 0: iterative recopy, another concurrent pass while the
         # dirty bytes shrink
-        c = (phos.Checkpoint(dp.table, phos.CKPT_COW, image.data_ptr(), image.numel(), chunk,
-                             4, staging.data_ptr(), staging_bytes, s) if mode == "cow" else
-             phos.Checkpoint(dp.table, phos.CKPT_RECOPY, image.data_ptr(), image.numel(), chunk,
-                             4, None, 0, s))
+        ns = {"sync": 0, "nosync": phos.CKPT_NO_SYNC,
+              "concurrent": phos.CKPT_CONCURRENT}[args.rounds]
+        c = (phos.Checkpoint(dp.table, phos.CKPT_COW | ns, image.data_ptr(), image.numel(),
+                             chunk, 4, staging.data_ptr(), staging_bytes, s) if mode == "cow" else
+             phos.Checkpoint(dp.table, phos.CKPT_RECOPY | ns, image.data_ptr(), image.numel(),
+                             chunk, 4, None, 0, s))
         k, prev, passes = 0, None, 0
         while k < len(dp.kernels):
             marks.mark("copier")
@@ -346,6 +351,11 @@ def run_gpu(args, rank, world):
     cow_ms = phase.get("cow", 0.0)
     cow_bytes = sum(a["cow_bytes"] for a, _ in stats)
     direct_bytes = sum(a["direct_bytes"] for a, _ in stats)
+    if args.rounds == "concurrent":
+        # the copier runs on its own stream, so the caller-stream phases do
+        # not bound its pieces: every device -> host byte of the step
+        # (copier, recopy, CoW direct copies) over the whole step time
+        d2h_gbs = (d2h_bytes + direct_bytes) / (ms * 1e6)
 
     # PCIe peak: DMA copy of 1 GiB to pinned memory, best of 5 (this run)
     g = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
@@ -442,7 +452,10 @@ def run_gpu(args, rank, world):
         legs = ("DMA engines (cudaMemcpyAsync) for pieces >= 1 MiB, k_copy_main for smaller "
                 "ones" if args.host_copy == "dma" else "k_copy_main (SM-issued stores)")
         roof = {"kernel": "host legs of the background copier and recopy, device -> pinned "
-                          "host: " + legs,
+                          "host: " + legs + (
+                              "; whole step (copier concurrent on its own stream)"
+                              if args.rounds == "concurrent" else
+                              "; copier and finish phases of the lockstep rounds"),
                 "bound": "pcie", "achieved": d2h_gbs, "peak": pcie_d2h, "unit": "GB/s",
                 "frac": d2h_gbs / pcie_d2h if pcie_d2h else None, "traffic": None,
                 "peak_source": "DMA cudaMemcpyAsync 1 GiB device->pinned, best of 5, "
@@ -458,6 +471,10 @@ def run_gpu(args, rank, world):
                        "chunk": chunk, "staging_bytes": staging_bytes,
                        "host_legs": ("DMA engines for pieces >= 1 MiB" if args.host_copy == "dma"
                                      else "SM copy kernel"),
+                       "rounds": {"sync": "host waits for each kernel's validation",
+                                  "nosync": "no wait per kernel, validation rule on the device",
+                                  "concurrent": "no wait per kernel, copier on its own stream "
+                                                "(event ordering)"}[args.rounds],
                        "l2": "inputs larger than L2 (image %.1f GB, traces %.2f GB)"
                              % (dp.image_bytes / 1e9, h2d / 1e9),
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -1093,6 +1110,90 @@ def run_priority(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+ROUNDS = ("per-round overhead of the lockstep protocol: the training-process table (1,000 "
+          "buffers, %.1f GB) with %d short kernels (65,536-record traces); one soft recopy "
+          "session (and one soft CoW session, staging image/20) whose copier moves image/2000 per "
+          "round in 4 MB pieces; lockstep rounds that wait for each validation, no-sync rounds "
+          "(rule on the device) and the concurrent copier (own stream), against the kernels "
+          "alone")
+
+
+def run_rounds(args, rank, world):
+    """Application kernels per second during a checkpoint: rounds that wait
+    for each kernel's validation vs rounds that only enqueue."""
+    import torch
+    from paper_2405_12079_b300 import phos, runner, workloads as wl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    s = torch.cuda.current_stream().cuda_stream
+    phos.host_copy_config(1 << 20)
+    n_k = 400
+    cfg = wl.training(scale=0.25 * args.scale, n_kernels=n_k)
+    rng, lay = cfg["rng"], cfg["layout"]
+    arena = torch.empty(lay.arena_bytes, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(arena.data_ptr(), lay.arena_bytes, cfg["seed"], s)
+    kernels = wl.make_training_kernels(rng, lay, arena.data_ptr(), n_k, 65536, 0.001)
+    dp = runner.DeviceProcess(lay, arena, cfg["seed"], kernels)
+    image = torch.empty(dp.image_bytes, dtype=torch.uint8).pin_memory()
+    staging = torch.empty(a256(dp.image_bytes / 20), dtype=torch.uint8, device="cuda")
+    quota = a256(dp.image_bytes / 2000)
+
+    def session(rounds, cow=False):
+        mode = (phos.CKPT_COW if cow else phos.CKPT_RECOPY) | {
+            "sync": 0, "nosync": phos.CKPT_NO_SYNC, "concurrent": phos.CKPT_CONCURRENT}[rounds]
+        c = phos.Checkpoint(dp.table, mode, image.data_ptr(), image.numel(), 4 << 20, 4,
+                            staging.data_ptr() if cow else None, staging.numel() if cow else 0, s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = 0
+        while k < n_k:
+            if c.advance(quota):
+                break
+            pk = dp.kernels[k]
+            c.before_kernel(pk.speculate(dp.table, dp.perm))
+            dp.run_kernel(k)
+            c.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
+            k += 1
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st = c.stats()
+        c.finish()
+        c.close()
+        return {"rounds": k, "ms_per_round": 1e3 * (t1 - t0) / k, "dirty": st["dirty"],
+                "copier_bytes": st["copier_bytes"]}
+
+    def alone():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_k):
+            dp.run_kernel(k)
+        torch.cuda.synchronize()
+        return {"rounds": n_k, "ms_per_round": 1e3 * (time.perf_counter() - t0) / n_k}
+
+    for r in ("sync", "nosync", "concurrent"):
+        session(r)
+    l0 = phos.launch_count()
+    res = {"kernels_alone": alone()}
+    for r in ("sync", "nosync", "concurrent"):
+        res["recopy_" + r] = session(r)
+        res["cow_" + r] = session(r, cow=True)
+    launches = phos.launch_count() - l0
+    assert res["recopy_sync"]["dirty"] == res["recopy_concurrent"]["dirty"]
+    best = res["recopy_concurrent"]
+    line = {"metric": METRIC, "value": 1e3 / best["ms_per_round"],
+            "unit": "kernel rounds/s", "higher_is_better": True, "n_gpus": world, "steps": 1,
+            "warmup": 1, "ms_per_step": best["ms_per_round"] * best["rounds"],
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": ROUNDS % (dp.image_bytes / 1e9, n_k)},
+            "arms": res,
+            "recopy_speedup_concurrent_vs_sync": res["recopy_sync"]["ms_per_round"] /
+            best["ms_per_round"],
+            "cow_speedup_concurrent_vs_sync": res["cow_sync"]["ms_per_round"] /
+            res["cow_concurrent"]["ms_per_round"], "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1101,10 +1202,13 @@ def main():
     ap.add_argument("--impl", default="phos", choices=["phos", "reference"])
     ap.add_argument("--workload", default="training",
                     choices=["training", "batched", "serving", "restore", "budget",
-                             "priority"],
+                             "priority", "rounds"],
                     help="training: the headline checkpoint step; batched: the 64-image plan")
     ap.add_argument("--host-copy", default="dma", choices=["sm", "dma"],
                     help="host legs on the SM copy kernel, or pieces >= 1 MiB on the DMA engines")
+    ap.add_argument("--rounds", default="concurrent", choices=["sync", "nosync", "concurrent"],
+                    help="nosync: protocol rounds do not wait for validation (device-side "
+                         "rule); concurrent: also the copier on its own stream")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (parity / quick runs); 1.0 = the full 40 GB")
     args = ap.parse_args()
@@ -1129,6 +1233,8 @@ def main():
         run_budget(args, rank, world)
     elif args.workload == "priority":
         run_priority(args, rank, world)
+    elif args.workload == "rounds":
+        run_rounds(args, rank, world)
     else:
         run_gpu(args, rank, world)
     if world > 1:

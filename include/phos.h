@@ -415,6 +415,31 @@ typedef struct phos_ckpt phos_ckpt_t;
 typedef struct phos_restore phos_restore_t;
 
 enum { PHOS_CKPT_COW = 1, PHOS_CKPT_RECOPY = 2 };
+/* OR'ed into phos_ckpt_desc_t.mode: after_kernel does not wait for the
+ * validation.  The protocol's response to it runs on the device instead
+ * (recopy: store victims in flight or done become dirty; CoW: the first
+ * round with a store victim neither done nor shadowed is recorded), so a
+ * round is enqueue-only and the host may run ahead of the device.  A CoW
+ * mis-speculation reaches the host through a mapped word: advance or
+ * after_kernel report it once visible (advance: done; after_kernel:
+ * *misspec = 1), and finish, which synchronises, copies every buffer
+ * stop-the-world at that point (later than the synchronous mode's
+ * fallback, which runs right after the kernel; both images are the memory
+ * of one instant).  Copies issued between the mis-speculation and its
+ * discovery are wasted but harmless.  stats and the dirty log synchronise
+ * first in this mode.  Results without a mis-speculation are identical to
+ * the synchronous mode's. */
+enum { PHOS_CKPT_NO_SYNC = 0x100 };
+/* OR'ed into mode (implies PHOS_CKPT_NO_SYNC): the background copier runs
+ * on a stream of its own, concurrently with the caller's kernels, instead
+ * of in lockstep on the caller's stream.  Each copier batch starts after
+ * the work the caller had enqueued before that advance call; a CoW kernel
+ * waits (stream event) only for the copier batches that still read a
+ * buffer it may write, or a staging extent it reuses; recopy kernels never
+ * wait (a buffer the copier touched and the kernel writes is dirty
+ * anyway).  Every host decision, and so every result, is the lockstep
+ * mode's. */
+enum { PHOS_CKPT_CONCURRENT = 0x200 };
 
 typedef struct {
     uint32_t mode;           /* PHOS_CKPT_COW (Sec. 4.2) or PHOS_CKPT_RECOPY
@@ -458,7 +483,7 @@ phos_status phos_ckpt_advance(phos_ckpt_t *c, uint64_t quota, int *done);
  * buffers that are in flight or done join the dirty set (Sec. 4.3). */
 phos_status phos_ckpt_before_kernel(phos_ckpt_t *c, const uint8_t *perm);
 /* Validate the kernel's trace (device, 16-byte aligned) against perm;
- * synchronises.  CoW: a store victim that was neither done nor shadowed
+ * synchronises (PHOS_CKPT_NO_SYNC: enqueues and returns).  CoW: a store victim that was neither done nor shadowed
  * before the kernel discards the checkpoint and copies every buffer
  * stop-the-world now; *misspec = 1 and the session is complete.  Recopy:
  * store victims that were in flight or done join the dirty set. */

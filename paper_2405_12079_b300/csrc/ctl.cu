@@ -6,6 +6,18 @@
 // stream.  Copy lists are staged in a pinned host arena and uploaded with
 // one asynchronous copy per batch; the arena is recycled at the stream
 // synchronisations that after_kernel performs anyway to read the victims.
+//
+// No-sync checkpoint sessions (PHOS_CKPT_NO_SYNC) take that round trip out:
+// after_kernel enqueues the validation and a one-CTA rule kernel that
+// applies the protocol's response on the device (recopy: store victims
+// that were in flight or done become dirty; CoW: the first round with a
+// store victim neither done nor shadowed is recorded and published to a
+// mapped host word), and returns at once.  Every host decision of a round
+// (copier pieces, CoW set, staging, dirty marks of speculated writes)
+// depends only on the speculation and on earlier host decisions, never on
+// a validation result, so the host can run ahead of the device; it learns
+// of a CoW mis-speculation from the mapped word at its next call, and at
+// the latest at finish, which then copies every buffer stop-the-world.
 #include <math.h>
 #include <string.h>
 
@@ -61,6 +73,43 @@ struct FirstFit {
     }
 };
 
+// One kernel's validation outcome applied on the device (no-sync sessions).
+// victim_st: the validation's store-victim bitmap; flags[i]: recopy, the
+// buffer was in flight or done when the kernel ran (touched); CoW, it was
+// done or shadowed (safe).  acc: u64[8] device words, [0..2] the
+// validation's counts, [3] running violation total, [4] first mis-speculated
+// round (-1 = none).  One CTA.
+__global__ void k_rule(const uint32_t *victim_st, const uint8_t *flags, uint32_t n, int cow,
+                       int64_t round, uint8_t *dirty, uint64_t *acc, int64_t *h_flag) {
+    __shared__ int hit;
+    if (threadIdx.x == 0) hit = 0;
+    __syncthreads();
+    const uint32_t nvw = (n + 31) / 32;
+    for (uint32_t w = threadIdx.x; w < nvw; w += blockDim.x) {
+        uint32_t v = victim_st[w];
+        while (v) {
+            const uint32_t i = w * 32 + (uint32_t)(__ffs(v) - 1);
+            v &= v - 1;
+            if (i >= n) break;
+            if (cow) {
+                if (!flags[i]) hit = 1;
+            } else if (flags[i]) {
+                dirty[i] = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        acc[3] += acc[0];
+        if (cow && hit && (int64_t)acc[4] < 0) {
+            // rounds run in stream order: the first one to get here wins
+            acc[4] = (uint64_t)round;
+            *(volatile int64_t *)h_flag = round;
+            __threadfence_system();
+        }
+    }
+}
+
 // Device and pinned resources shared by the sessions.
 struct Session {
     const phos_table *t = nullptr;
@@ -88,6 +137,25 @@ struct Session {
     uint64_t round = 0;
     std::vector<uint64_t> copier_log;
     uint64_t validated = 0, violations = 0;
+    // no-sync sessions: per-round perm | flags slots in a pinned upload
+    // arena (recycled at synchronisations), validation outputs and rule
+    // state in device memory, the mis-speculation word mapped
+    bool nosync = false;
+    uint8_t *h_up = nullptr, *d_up = nullptr;
+    size_t up_cap = 0, up_used = 0, slot = 0;
+    uint64_t *d_acc = nullptr;      // u64[8], see k_rule
+    uint32_t *d_vic = nullptr;      // victim | victim_st
+    uint8_t *d_dirty = nullptr;     // u8[n]
+    int64_t *h_flag = nullptr, *d_flag = nullptr;
+    // concurrent sessions: the copier's own stream, a clone of the table
+    // (its own copy-engine scratch), one event per copier batch (ring)
+    static constexpr uint32_t kRing = 64;
+    cudaStream_t cs = nullptr;
+    phos_table_t *tc = nullptr;
+    cudaEvent_t app_ev = nullptr;
+    cudaEvent_t bev[kRing] = {};
+    uint64_t batch = 0;                 // copier batches issued on cs
+    std::vector<uint64_t> last_batch;   // per buffer: batch of its last piece
 
     phos_status init(const phos_table *tt, cudaStream_t ss, uint32_t ww, uint64_t ch) {
         t = tt;
@@ -110,8 +178,88 @@ struct Session {
         return reserve_list(1024);
     }
 
+    phos_status init_nosync() {
+        nosync = true;
+        const uint32_t nvw = std::max((n + 31) / 32, 1u);
+        PHOS_CUDA(cudaMalloc(&d_acc, 64));
+        PHOS_CUDA(cudaMalloc(&d_vic, 8ull * nvw));
+        PHOS_CUDA(cudaMalloc(&d_dirty, std::max(n, 1u)));
+        PHOS_CUDA(cudaHostAlloc(&h_flag, 64, cudaHostAllocMapped));
+        PHOS_CUDA(cudaHostGetDevicePointer((void **)&d_flag, h_flag, 0));
+        *(volatile int64_t *)h_flag = -1;
+        uint64_t a0[8] = {0, 0, 0, 0, ~0ull, 0, 0, 0};
+        PHOS_CUDA(cudaMemcpy(d_acc, a0, sizeof a0, cudaMemcpyHostToDevice));
+        PHOS_CUDA(cudaMemset(d_dirty, 0, std::max(n, 1u)));
+        return reserve_list(65536);
+    }
+
+    phos_status init_concurrent() {
+        phos_status r = init_nosync();
+        if (r) return r;
+        PHOS_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        std::vector<phos_buf_t> b(n);
+        for (uint32_t i = 0; i < n; ++i) b[i] = phos_buf_t{t->base[i], t->size[i]};
+        r = phos_table_create(b.data(), n, &tc);
+        if (r) return r;
+        PHOS_CUDA(cudaEventCreateWithFlags(&app_ev, cudaEventDisableTiming));
+        for (cudaEvent_t &e : bev) PHOS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        last_batch.assign(n, 0);
+        return PHOS_OK;
+    }
+
+    // Both streams (the upload and list arenas are shared by them).
+    cudaError_t sync_streams() {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && cs) e = cudaStreamSynchronize(cs);
+        return e;
+    }
+
+    // Make the caller's stream wait for copier batch b (an event of the
+    // ring; a newer batch in the same slot only waits longer).
+    phos_status app_wait(uint64_t b) {
+        if (b) PHOS_CUDA(cudaStreamWaitEvent(s, bev[b % kRing], 0));
+        return PHOS_OK;
+    }
+
+    // A 256-aligned slot of `bytes` in the upload arena.
+    phos_status alloc_up(size_t bytes, size_t *off) {
+        bytes = align_up(std::max<size_t>(bytes, 1), 256);
+        if (up_used + bytes > up_cap) {
+            PHOS_CUDA(sync_streams());
+            h_used = 0;
+            up_used = 0;
+            if (bytes > up_cap) {
+                if (h_up) cudaFreeHost(h_up);
+                if (d_up) cudaFree(d_up);
+                h_up = nullptr;
+                d_up = nullptr;
+                const size_t cap = std::max<size_t>({bytes * 64, 2 * up_cap, 1 << 20});
+                PHOS_CUDA(cudaHostAlloc(&h_up, cap, cudaHostAllocDefault));
+                PHOS_CUDA(cudaMalloc(&d_up, cap));
+                up_cap = cap;
+            }
+        }
+        *off = up_used;
+        up_used += bytes;
+        return PHOS_OK;
+    }
+
     ~Session() {
         if (s) cudaStreamSynchronize(s);
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        if (tc) phos_table_destroy(tc);
+        if (app_ev) cudaEventDestroy(app_ev);
+        for (cudaEvent_t e : bev)
+            if (e) cudaEventDestroy(e);
+        if (h_up) cudaFreeHost(h_up);
+        if (d_up) cudaFree(d_up);
+        if (d_acc) cudaFree(d_acc);
+        if (d_vic) cudaFree(d_vic);
+        if (d_dirty) cudaFree(d_dirty);
+        if (h_flag) cudaFreeHost(h_flag);
         if (h_list) cudaFreeHost(h_list);
         if (d_list) cudaFree(d_list);
         if (h_perm) cudaFreeHost(h_perm);
@@ -126,7 +274,7 @@ struct Session {
         if (need <= h_cap) return PHOS_OK;
         size_t cap = std::max(need, 2 * h_cap);
         if (h_list) {
-            PHOS_CUDA(cudaStreamSynchronize(s));
+            PHOS_CUDA(sync_streams());
             cudaFreeHost(h_list);
             cudaFree(d_list);
             h_used = 0;
@@ -142,9 +290,15 @@ struct Session {
     // first; their present marks ride in the kernel batch that follows on
     // the same stream (a zero-length descriptor), so no bit precedes its
     // bytes.
+    // copier = true in a concurrent session: on the copier's stream, through
+    // the table clone.
     phos_status submit(const std::vector<phos_copy_t> &v0, void *staging, uint64_t staging_bytes,
-                       const void *image, uint64_t image_bytes, uint32_t *present) {
+                       const void *image, uint64_t image_bytes, uint32_t *present,
+                       bool copier = false) {
         if (v0.empty()) return PHOS_OK;
+        const bool on_cs = copier && cs;
+        const cudaStream_t st = on_cs ? cs : s;
+        const phos_table_t *tt = on_cs ? tc : t;
         std::vector<phos_copy_t> keep;
         const std::vector<phos_copy_t> *vp = &v0;
         if (g_dma_min) {
@@ -170,7 +324,7 @@ struct Session {
                     src = static_cast<const uint8_t *>(image) + d.src_off;
                     dst = reinterpret_cast<uint8_t *>(t->base[d.buf] + d.dst_off);
                 }
-                PHOS_CUDA(cudaMemcpyAsync(dst, src, d.len, cudaMemcpyDefault, s));
+                PHOS_CUDA(cudaMemcpyAsync(dst, src, d.len, cudaMemcpyDefault, st));
                 if (d.flags & PHOS_COPY_MARK_PRESENT) {
                     phos_copy_t m = d;
                     m.len = 0;
@@ -184,7 +338,7 @@ struct Session {
         }
         const std::vector<phos_copy_t> &v = *vp;
         if (h_used + v.size() > h_cap) {
-            PHOS_CUDA(cudaStreamSynchronize(s));
+            PHOS_CUDA(sync_streams());
             h_used = 0;
             phos_status r = reserve_list(v.size());
             if (r) return r;
@@ -193,23 +347,31 @@ struct Session {
         phos_copy_t *dp = d_list + h_used;
         memcpy(hp, v.data(), v.size() * sizeof(phos_copy_t));
         PHOS_CUDA(cudaMemcpyAsync(dp, hp, v.size() * sizeof(phos_copy_t), cudaMemcpyHostToDevice,
-                                  s));
+                                  st));
         h_used += v.size();
-        return phos_copy(t, dp, (uint32_t)v.size(), staging, staging_bytes,
-                         const_cast<void *>(image), image_bytes, present, d_status, s);
+        return phos_copy(tt, dp, (uint32_t)v.size(), staging, staging_bytes,
+                         const_cast<void *>(image), image_bytes, present, d_status, st);
     }
 
     phos_status sync() {
-        PHOS_CUDA(cudaStreamSynchronize(s));
+        PHOS_CUDA(sync_streams());
         h_used = 0;
+        up_used = 0;
         if (*h_status) return fail((phos_status)*h_status, "device reported %s",
                                    phos_status_name((phos_status)*h_status));
         return PHOS_OK;
     }
 
-    // perm for the next kernel -> device
+    // perm for the next kernel -> device (no-sync: into this round's slot,
+    // uploaded with the round's flags by upload_slot)
     phos_status stage_perm(const uint8_t *perm) {
         if (!perm && n) return fail(PHOS_EINVAL, "perm is NULL");
+        if (nosync) {
+            phos_status r = alloc_up(2ull * n, &slot);
+            if (r) return r;
+            if (n) memcpy(h_up + slot, perm, n);
+            return PHOS_OK;
+        }
         if (n) {
             memcpy(h_perm, perm, n);
             PHOS_CUDA(cudaMemcpyAsync(d_perm, h_perm, n, cudaMemcpyHostToDevice, s));
@@ -217,15 +379,68 @@ struct Session {
         return PHOS_OK;
     }
 
-    // Validate and wait: fills h_count and h_victim (victim | victim_st).
-    phos_status validate_sync(const uint64_t *d_trace, uint64_t n_rec) {
+    phos_status upload_slot(const std::vector<uint8_t> &flags) {
+        if (!n) return PHOS_OK;
+        memcpy(h_up + slot + n, flags.data(), n);
+        PHOS_CUDA(cudaMemcpyAsync(d_up + slot, h_up + slot, 2ull * n, cudaMemcpyHostToDevice, s));
+        return PHOS_OK;
+    }
+
+    phos_status bitmap_for(uint64_t n_rec) {
         const uint64_t words = std::max<uint64_t>((n_rec + 31) / 32, 1);
         if (words > bitmap_words) {
-            PHOS_CUDA(cudaStreamSynchronize(s));
+            PHOS_CUDA(sync_streams());
+            h_used = 0;
+            up_used = 0;
             if (d_bitmap) cudaFree(d_bitmap);
             PHOS_CUDA(cudaMalloc(&d_bitmap, words * 4));
             bitmap_words = words;
         }
+        return PHOS_OK;
+    }
+
+    // Validate and apply the rule on the device; returns without waiting.
+    phos_status validate_nosync(const uint64_t *d_trace, uint64_t n_rec, bool cow) {
+        // growth synchronises: this round's slot is uploaded by then and
+        // later uploads into its device copy are stream-ordered after the
+        // validation below
+        phos_status r0 = bitmap_for(n_rec);
+        if (r0) return r0;
+        const uint32_t nvw = std::max((n + 31) / 32, 1u);
+        phos_status r = phos_validate(t, d_up + slot, d_trace, n_rec, w, d_bitmap, d_acc, d_vic,
+                                      d_vic + nvw, nullptr, 0, d_status, s);
+        if (r) return r;
+        k_rule<<<1, 256, 0, s>>>(d_vic + nvw, d_up + slot + n, n, cow ? 1 : 0,
+                                 (int64_t)round - 1, d_dirty, d_acc, d_flag);
+        PHOS_CUDA(cudaGetLastError());
+        count_launch();
+        validated += n_rec;
+        return PHOS_OK;
+    }
+
+    // No-sync: wait, then fold the device's violation total and dirty marks
+    // into the host state (the device dirty marks are cleared).
+    phos_status collect(std::vector<uint8_t> *dirty) {
+        phos_status r = sync();
+        if (r) return r;
+        uint64_t acc[8];
+        PHOS_CUDA(cudaMemcpy(acc, d_acc, sizeof acc, cudaMemcpyDeviceToHost));
+        violations = acc[3];
+        if (dirty && n) {
+            std::vector<uint8_t> dd(n);
+            PHOS_CUDA(cudaMemcpy(dd.data(), d_dirty, n, cudaMemcpyDeviceToHost));
+            for (uint32_t i = 0; i < n; ++i) (*dirty)[i] |= dd[i];
+            PHOS_CUDA(cudaMemset(d_dirty, 0, n));
+        }
+        return PHOS_OK;
+    }
+
+    int64_t flag() const { return *(volatile const int64_t *)h_flag; }
+
+    // Validate and wait: fills h_count and h_victim (victim | victim_st).
+    phos_status validate_sync(const uint64_t *d_trace, uint64_t n_rec) {
+        phos_status r0 = bitmap_for(n_rec);
+        if (r0) return r0;
         const uint32_t nvw = (n + 31) / 32;
         phos_status r = phos_validate(t, d_perm, d_trace, n_rec, w, d_bitmap, d_count, d_victim,
                                       d_victim + std::max(nvw, 1u), nullptr, 0, d_status, s);
@@ -318,13 +533,17 @@ struct phos_ckpt {
     uint64_t cow_bytes = 0, direct_bytes = 0, copier_bytes = 0, recopy_bytes = 0;
     int64_t misspec = -1;
     bool complete = false, finished = false, in_kernel = false;
+    // concurrent: copier batch of the last staging release, and the latest
+    // release batch the caller's stream has waited for
+    uint64_t release_batch = 0, waited_release = 0;
 };
 
 extern "C" phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_desc_t *d,
                                        phos_stream_t stream, phos_ckpt_t **out) {
     if (!t || !d || !out) return fail(PHOS_EINVAL, "ckpt_begin: NULL argument");
     *out = nullptr;
-    if (d->mode != PHOS_CKPT_COW && d->mode != PHOS_CKPT_RECOPY)
+    const uint32_t mode = d->mode & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT);
+    if (mode != PHOS_CKPT_COW && mode != PHOS_CKPT_RECOPY)
         return fail(PHOS_EINVAL, "ckpt_begin: mode %u", d->mode);
     if (d->access_bytes == 0 || d->chunk == 0 || d->chunk % 256)
         return fail(PHOS_EINVAL, "ckpt_begin: access_bytes >= 1, chunk a multiple of 256");
@@ -337,8 +556,16 @@ extern "C" phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_de
         delete c;
         return r;
     }
-    c->mode = d->mode;
-    c->staging = d->mode == PHOS_CKPT_COW ? d->d_staging : nullptr;
+    if ((d->mode & PHOS_CKPT_CONCURRENT) && (r = c->ss.init_concurrent())) {
+        delete c;
+        return r;
+    }
+    if ((d->mode & PHOS_CKPT_NO_SYNC) && !c->ss.nosync && (r = c->ss.init_nosync())) {
+        delete c;
+        return r;
+    }
+    c->mode = mode;
+    c->staging = mode == PHOS_CKPT_COW ? d->d_staging : nullptr;
     c->staging_bytes = c->staging ? d->staging_bytes : 0;
     c->image = d->image;
     c->image_bytes = d->image_bytes;
@@ -356,6 +583,14 @@ static phos_status ckpt_advance(phos_ckpt *c, uint64_t quota) {
     Session &S = c->ss;
     const phos_table *t = S.t;
     std::vector<phos_copy_t> v;
+    // concurrent: this batch runs on the copier's stream after everything
+    // the caller has enqueued so far (the previous kernels and their CoW
+    // copies); the kernels that follow wait for it only where they write
+    const uint64_t b = S.batch + 1;
+    if (S.cs) {
+        PHOS_CUDA(cudaEventRecord(S.app_ev, S.s));
+        PHOS_CUDA(cudaStreamWaitEvent(S.cs, S.app_ev, 0));
+    }
     uint64_t moved = S.advance(
         quota,
         [&](uint32_t i, uint64_t off, uint64_t len) {
@@ -372,22 +607,37 @@ static phos_status ckpt_advance(phos_ckpt *c, uint64_t quota) {
                 d.flags = PHOS_COPY_LIVE_TO_IMAGE;
             }
             v.push_back(d);
+            if (S.cs) S.last_batch[i] = b;
             if (off + len == t->size[i] && sh >= 0) {
-                // the drain is stream-ordered before any later reuse
+                // the drain is stream-ordered before any later reuse (on
+                // the copier's stream: a CoW copy into the extent waits
+                // for this batch first)
                 c->alloc.release((uint64_t)sh, align_up(t->size[i], 256));
                 c->shadow[i] = -1;
+                c->release_batch = b;
             }
             return sh >= 0;
         },
         [](uint32_t) { return false; });
     c->copier_bytes += moved;
-    return S.submit(v, c->staging, c->staging_bytes, c->image, c->image_bytes, nullptr);
+    phos_status r = S.submit(v, c->staging, c->staging_bytes, c->image, c->image_bytes, nullptr,
+                             true);
+    if (r) return r;
+    if (S.cs && !v.empty()) {
+        S.batch = b;
+        PHOS_CUDA(cudaEventRecord(S.bev[b % Session::kRing], S.cs));
+    }
+    return PHOS_OK;
 }
 
 extern "C" phos_status phos_ckpt_advance(phos_ckpt_t *c, uint64_t quota, int *done) {
     if (!c) return fail(PHOS_EINVAL, "ckpt_advance: NULL session");
     if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_advance: inside a kernel round");
     phos_status r = PHOS_OK;
+    if (c->ss.nosync && c->mode == PHOS_CKPT_COW && !c->complete && c->ss.flag() >= 0) {
+        c->misspec = c->ss.flag();        // the device saw it; finish falls back
+        c->complete = true;
+    }
     if (!c->complete) {
         r = ckpt_advance(c, quota);
         if (c->ss.done()) c->complete = true;
@@ -406,6 +656,19 @@ extern "C" phos_status phos_ckpt_before_kernel(phos_ckpt_t *c, const uint8_t *pe
     if (r) return r;
     const uint32_t n = S.n;
     if (c->mode == PHOS_CKPT_COW) {
+        if (S.cs) {
+            // the kernel may not overwrite a buffer the copier still reads
+            // live, nor a CoW copy land in staging a drain still reads
+            uint64_t need = 0;
+            for (uint32_t i = 0; i < n; ++i)
+                if (perm[i] & PHOS_PERM_W) need = std::max(need, S.last_batch[i]);
+            if (c->release_batch > c->waited_release) {
+                need = std::max(need, c->release_batch);
+                c->waited_release = c->release_batch;
+            }
+            r = S.app_wait(need);
+            if (r) return r;
+        }
         std::vector<phos_copy_t> v;
         for (uint32_t i = 0; i < n; ++i) {
             if (!(perm[i] & PHOS_PERM_W)) continue;
@@ -438,11 +701,13 @@ extern "C" phos_status phos_ckpt_before_kernel(phos_ckpt_t *c, const uint8_t *pe
         for (uint32_t i = 0; i < n; ++i) c->safe[i] = S.state[i] == kDone || c->shadow[i] >= 0;
         r = S.submit(v, c->staging, c->staging_bytes, c->image, c->image_bytes, nullptr);
         if (r) return r;
+        if (S.nosync && (r = S.upload_slot(c->safe))) return r;
     } else {
         for (uint32_t i = 0; i < n; ++i) {
             c->touched[i] = S.state[i] != kPending;
             if ((perm[i] & PHOS_PERM_W) && c->touched[i]) c->dirty[i] = 1;
         }
+        if (S.nosync && (r = S.upload_slot(c->touched))) return r;
     }
     c->in_kernel = true;
     return PHOS_OK;
@@ -475,6 +740,16 @@ extern "C" phos_status phos_ckpt_after_kernel(phos_ckpt_t *c, const uint64_t *d_
     c->in_kernel = false;
     const uint64_t k = S.round++;
     if (misspec) *misspec = 0;
+    if (S.nosync) {
+        phos_status r = S.validate_nosync(d_trace, n_rec, c->mode == PHOS_CKPT_COW);
+        if (r) return r;
+        if (c->mode == PHOS_CKPT_COW && S.flag() >= 0) {
+            c->misspec = S.flag();
+            c->complete = true;
+            if (misspec) *misspec = 1;
+        }
+        return PHOS_OK;
+    }
     phos_status r = S.validate_sync(d_trace, n_rec);
     if (r) return r;
     if (S.h_count[1] == 0) return PHOS_OK;  // no store violated the speculation
@@ -503,11 +778,26 @@ extern "C" phos_status phos_ckpt_finish(phos_ckpt_t *c) {
     if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_finish: inside a kernel round");
     Session &S = c->ss;
     phos_status r;
+    if (S.nosync && !c->finished) {
+        // everything enqueued has run: the rule's outcome is final
+        r = S.collect(c->mode == PHOS_CKPT_RECOPY ? &c->dirty : nullptr);
+        if (r) return r;
+        if (c->mode == PHOS_CKPT_COW && S.flag() >= 0) {
+            // mis-speculation: discard, copy everything stop-the-world now
+            c->misspec = S.flag();
+            r = stw_checkpoint(c);
+            if (r) return r;
+            c->complete = true;
+            std::fill(c->shadow.begin(), c->shadow.end(), -1);
+        }
+    }
     if (!c->complete && c->misspec < 0) {
         r = ckpt_advance(c, ~0ull >> 2);
         if (r) return r;
         c->complete = S.done();
     }
+    // concurrent: the recopy below lands after every copier piece
+    if (S.cs && (r = S.app_wait(S.batch))) return r;
     if (c->mode == PHOS_CKPT_RECOPY && !c->finished) {
         // t2: quiesce (the caller has stopped issuing kernels), recopy the
         // dirty buffers whole from live memory
@@ -537,6 +827,10 @@ extern "C" phos_status phos_ckpt_begin_pass(phos_ckpt_t *c, uint64_t *pass_bytes
         return fail(PHOS_EINVAL, "ckpt_begin_pass: inside a kernel round or finished");
     Session &S = c->ss;
     if (!S.done()) return fail(PHOS_EINVAL, "ckpt_begin_pass: the current pass is not done");
+    if (S.nosync) {
+        phos_status r = S.collect(&c->dirty);
+        if (r) return r;
+    }
     uint64_t bytes = 0, nb = 0;
     for (uint32_t i = 0; i < S.n; ++i) {
         if (!c->dirty[i]) continue;
@@ -553,8 +847,19 @@ extern "C" phos_status phos_ckpt_begin_pass(phos_ckpt_t *c, uint64_t *pass_bytes
     return PHOS_OK;
 }
 
+// No-sync sessions: bring the device-side dirty marks and violation total
+// into the host state before reporting them.
+static phos_status ckpt_collect(const phos_ckpt_t *cc) {
+    phos_ckpt *c = const_cast<phos_ckpt *>(cc);
+    if (!c->ss.nosync || c->finished) return PHOS_OK;
+    return c->ss.collect(c->mode == PHOS_CKPT_RECOPY ? &c->dirty : nullptr);
+}
+
 extern "C" phos_status phos_ckpt_stats(const phos_ckpt_t *c, phos_ckpt_stats_t *o) {
     if (!c || !o) return fail(PHOS_EINVAL, "ckpt_stats: NULL argument");
+    if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_stats: inside a kernel round");
+    phos_status r = ckpt_collect(c);
+    if (r) return r;
     memset(o, 0, sizeof *o);
     o->kernels = c->ss.round;
     o->copier_bytes = c->copier_bytes;
@@ -578,6 +883,9 @@ extern "C" phos_status phos_ckpt_log(const phos_ckpt_t *c, uint32_t kind, uint64
     if (kind == 0) return copy_log(c->cow_log, out, cap, n_out);
     if (kind == 1) return copy_log(c->ss.copier_log, out, cap, n_out);
     if (kind == 2) {
+        if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_log: inside a kernel round");
+        phos_status r = ckpt_collect(c);
+        if (r) return r;
         std::vector<uint64_t> v;
         for (uint32_t i = 0; i < c->ss.n; ++i)
             if (c->dirty[i]) v.insert(v.end(), {i, 0, 0, 0, 0});

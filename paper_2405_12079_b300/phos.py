@@ -92,6 +92,8 @@ _SIGS = {
 }
 
 CKPT_COW, CKPT_RECOPY = 1, 2
+CKPT_NO_SYNC = 0x100
+CKPT_CONCURRENT = 0x200
 
 
 REQ_CHECKPOINT, REQ_RESTORE = 1, 2

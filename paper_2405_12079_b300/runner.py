@@ -72,15 +72,24 @@ class DeviceProcess:
         phos.harness_mutate(self.table, self.seed, k, pk.reads, pk.writes,
                             pk.d_strays.data_ptr(), pk.ns, self.stream())
 
-    def run_cow(self, image, quota, chunk, staging=None, staging_bytes=0):
-        return self._ckpt(phos.CKPT_COW, image, quota, chunk, staging, staging_bytes)
+    @staticmethod
+    def _flags(rounds):
+        """rounds: "sync" (wait for each validation), "nosync" (rule on the
+        device) or "concurrent" (nosync, copier on its own stream)."""
+        return {"sync": 0, "nosync": phos.CKPT_NO_SYNC,
+                "concurrent": phos.CKPT_CONCURRENT}[rounds]
 
-    def run_recopy(self, image, quota, chunk, max_passes=0, stop_bytes=0):
+    def run_cow(self, image, quota, chunk, staging=None, staging_bytes=0, rounds="sync"):
+        """Soft copy-on-write."""
+        return self._ckpt(phos.CKPT_COW | self._flags(rounds), image, quota, chunk, staging,
+                          staging_bytes)
+
+    def run_recopy(self, image, quota, chunk, max_passes=0, stop_bytes=0, rounds="sync"):
         """Soft recopy; with max_passes > 0, iterative: each time the copier
         finishes a pass, another concurrent pass recopies the dirty set while
         its bytes exceed stop_bytes and keep shrinking."""
-        return self._ckpt(phos.CKPT_RECOPY, image, quota, chunk, None, 0, max_passes,
-                          stop_bytes)
+        return self._ckpt(phos.CKPT_RECOPY | self._flags(rounds), image, quota, chunk, None, 0,
+                          max_passes, stop_bytes)
 
     def _ckpt(self, mode, image, quota, chunk, staging, staging_bytes, max_passes=0,
               stop_bytes=0):

@@ -65,20 +65,20 @@ def training_world(seed, scale, n_kernels, stray_store_frac=0.0):
     return World(cfg["layout"], seed, mk), cfg
 
 
-def check_ckpt(w, mode, quota, chunk, staging_bytes=0):
+def check_ckpt(w, mode, quota, chunk, staging_bytes=0, rounds="sync"):
     img = torch.zeros(w.dp.image_bytes, dtype=torch.uint8).pin_memory()
     stg = torch.zeros(max(staging_bytes, 256), dtype=torch.uint8, device="cuda")
     proc = w.oracle_proc()
     if mode == "cow":
         exp = P.cow_checkpoint(proc, w.kernels, staging_bytes, chunk, quota)
-        got = w.dp.run_cow(img, quota, chunk, stg, staging_bytes)
+        got = w.dp.run_cow(img, quota, chunk, stg, staging_bytes, rounds=rounds)
         assert got["stats"]["misspec_round"] == (-1 if exp.misspec is None else exp.misspec)
         assert [tuple(int(x) for x in r) for r in got["cow"]] == cow_rows(exp.cow_log)
         assert got["stats"]["cow_bytes"] == exp.stats["cow_bytes"]
         assert got["stats"]["direct_bytes"] == exp.stats["direct_bytes"]
     else:
         exp = P.recopy_checkpoint(proc, w.kernels, chunk, quota)
-        got = w.dp.run_recopy(img, quota, chunk)
+        got = w.dp.run_recopy(img, quota, chunk, rounds=rounds)
         assert got["dirty"].tolist() == exp.dirty
         assert got["stats"]["recopy_bytes"] == exp.stats["recopy_bytes"]
     torch.cuda.synchronize()
@@ -89,13 +89,17 @@ def check_ckpt(w, mode, quota, chunk, staging_bytes=0):
     return got, exp
 
 
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent"])
 @pytest.mark.parametrize("mode", ["cow", "recopy"])
-def test_training_image_scaled(mode):
+def test_training_image_scaled(mode, rounds):
     """Training-process shape at 1/500 scale (1,000 buffers, ~80 MB,
-    200 kernels); quota = image/100, chunk 64 KiB, staging 4 MB."""
+    200 kernels); quota = image/100, chunk 64 KiB, staging 4 MB.  The
+    no-sync rounds (rule on the device, no wait per kernel) and the
+    concurrent copier (its own stream, event ordering) give exactly the
+    lockstep results."""
     w, cfg = training_world(wl.SEED0 + 2, 0.002, 200)
     quota = a256(w.dp.image_bytes / 100)
-    got, exp = check_ckpt(w, mode, quota, 64 * 1024, staging_bytes=4 << 20)
+    got, exp = check_ckpt(w, mode, quota, 64 * 1024, staging_bytes=4 << 20, rounds=rounds)
     if mode == "cow":
         assert len(exp.cow_log) > 0 and exp.misspec is None
     else:
@@ -111,6 +115,42 @@ def test_stray_stores_fault_injection(mode):
     got, exp = check_ckpt(w, mode, quota, 32 * 1024, staging_bytes=1 << 20)
     if mode == "cow":
         assert exp.misspec is not None
+
+
+@pytest.mark.parametrize("rounds", ["nosync", "concurrent"])
+def test_stray_stores_recopy_nosync(rounds):
+    """Recopy without a wait per kernel: the store victims reach the dirty
+    set through the device-side rule; everything equals the oracle."""
+    w, cfg = training_world(wl.SEED0 + 12, 0.001, 80, stray_store_frac=0.3)
+    quota = a256(w.dp.image_bytes / 60)
+    got, exp = check_ckpt(w, "recopy", quota, 32 * 1024, rounds=rounds)
+    assert got["stats"]["violations"] > 0
+
+
+@pytest.mark.parametrize("rounds", ["nosync", "concurrent"])
+def test_stray_stores_cow_nosync_falls_back_at_finish(rounds):
+    """CoW without a wait per kernel on the mis-speculating workload: the
+    device records the same first mis-speculated round as the oracle; the
+    host learns of it later, so more kernels run before the stop-the-world
+    copy, and the image equals live memory at finish, which equals the
+    oracle's memory after that many kernels."""
+    w, cfg = training_world(wl.SEED0 + 12, 0.001, 80, stray_store_frac=0.3)
+    quota = a256(w.dp.image_bytes / 60)
+    chunk = 32 * 1024
+    img = torch.zeros(w.dp.image_bytes, dtype=torch.uint8).pin_memory()
+    stg = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    exp = P.cow_checkpoint(w.oracle_proc(), w.kernels, 1 << 20, chunk, quota)
+    assert exp.misspec is not None
+    got = w.dp.run_cow(img, quota, chunk, stg, 1 << 20, rounds=rounds)
+    torch.cuda.synchronize()
+    assert got["stats"]["misspec_round"] == exp.misspec
+    k_run = got["kernels_run"]
+    assert k_run >= exp.kernels_run
+    proc = w.oracle_proc()
+    for k in range(k_run):
+        proc.run_kernel(k, w.kernels[k])
+    assert w.live_equal(proc)
+    assert np.array_equal(img.numpy(), P.stw_checkpoint(proc))
 
 
 def test_cow_budget_zero_and_tiny_config():
@@ -188,7 +228,8 @@ def test_restore_stray_load_rolls_back():
 @pytest.mark.parametrize("div,n_kernels,stray,max_passes,stop", [
     (100, 200, 0.0, 6, 0), (30, 200, 0.0, 6, 0), (30, 200, 0.0, 1, 0),
     (20, 120, 0.3, 6, 1 << 20)])
-def test_iterative_recopy(div, n_kernels, stray, max_passes, stop):
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent"])
+def test_iterative_recopy(div, n_kernels, stray, max_passes, stop, rounds):
     """Iterative concurrent recopy (Sec. 4.3): the passes (round, buffers,
     bytes), the copier pieces across passes, the final dirty set, the image
     at t2 and live memory all equal the oracle's; the stop-the-world recopy
@@ -200,7 +241,8 @@ def test_iterative_recopy(div, n_kernels, stray, max_passes, stop):
     img = torch.zeros(w.dp.image_bytes, dtype=torch.uint8).pin_memory()
     proc = w.oracle_proc()
     exp = P.iterative_recopy(proc, w.kernels, chunk, quota, max_passes, stop)
-    got = w.dp.run_recopy(img, quota, chunk, max_passes=max_passes, stop_bytes=stop)
+    got = w.dp.run_recopy(img, quota, chunk, max_passes=max_passes, stop_bytes=stop,
+                          rounds=rounds)
     torch.cuda.synchronize()
     assert len(exp.passes) >= 1
     assert [(int(r), int(nb), int(b)) for r, nb, b, _, _ in got["passes"]] == \
