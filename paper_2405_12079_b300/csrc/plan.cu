@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(const PlanDev P) {
             __syncwarp();
             uint32_t *bm = it.bitmap + (r0 >> 5);
             if (nb == kBatch)
-                batch_words<true, true>(L, recs, nb, 32, lane, mine, bm, sv, svs, acc);
+                batch_pairs<true>(L, recs, 32, lane, mine, bm, sv, svs, acc);
             else
                 batch_words<true, false>(L, recs, nb, 32, lane, mine, bm, sv, svs, acc);
             __syncwarp();

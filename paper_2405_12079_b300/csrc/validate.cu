@@ -332,8 +332,8 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
     const uint32_t n = p.tab.n, nvw = p.nvw;
-    Lead *leads = reinterpret_cast<Lead *>(smem);             // [nwarps][32]
-    uint8_t *cur = smem + sizeof(Lead) * 32 * nwarps;
+    Lead *leads = reinterpret_cast<Lead *>(smem);             // [nwarps][2][32]
+    uint8_t *cur = smem + sizeof(Lead) * 64 * nwarps;
     unsigned long long *red = reinterpret_cast<unsigned long long *>(cur);
     uint32_t *last = reinterpret_cast<uint32_t *>(cur + 24);
     cur += 32;
@@ -376,9 +376,74 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     const uint64_t brec = 32ull * W;
     const uint64_t nbatch = (p.n_rec + brec - 1) / brec;
     const uint64_t b0 = nbatch * c / G, b1 = nbatch * (c + 1) / G;
-    Lead *mine = leads + 32 * warp;
+    const uint64_t nfull = p.n_rec / brec;
+    Lead *mine = leads + 64 * warp;
     Acc acc;
-    for (uint64_t bt = b0 + warp; bt < b1; bt += nwarps) {
+    uint64_t bt = b0 + warp;
+    // Full batches run as one stream per warp: the leader records of the
+    // warp's next batch are loaded a batch ahead and the record ring runs on
+    // into that batch's first pairs, so no batch begins with a load the warp
+    // has to wait for.  Two leader sets per warp alternate.
+    {
+        const uint32_t npair = W >> 1;           // W is 8, 16 or 32
+        const ulonglong2 z = make_ulonglong2(0, 0);
+        ulonglong2 r[4];
+        uint64_t xl = 0;
+        if (bt < b1 && bt < nfull) {
+            const uint64_t *rc = p.trace + bt * brec;
+            xl = lane < W ? rc[lane * 32] : 0ull;
+            const ulonglong2 *pc = reinterpret_cast<const ulonglong2 *>(rc) + lane;
+#pragma unroll
+            for (uint32_t u = 0; u < 3; ++u) r[u] = u < npair ? pc[u * 32] : z;
+        }
+        uint32_t sel = 0;
+        const uint32_t half = lane >> 4;
+        while (bt < b1 && bt < nfull) {
+            const uint64_t nt = bt + nwarps;
+            const bool more = nt < b1 && nt < nfull;
+            Lead *ldp = mine + 32 * sel;
+            {
+                Lead ld;
+                ld.b = 0;
+                ld.l = 0;
+                ld.i = -1;
+                ld.pm = 0;
+                if (lane < W) {
+                    const int i = L.lane_search(xl & PHOS_REC_ADDR_MASK);
+                    if (i >= 0) {
+                        ld.b = L.base[i];
+                        ld.l = L.limit(i, kSmemTable);
+                        ld.i = i;
+                        ld.pm = L.perm[i];
+                    }
+                }
+                ldp[lane] = ld;
+            }
+            const uint64_t *rn = p.trace + (more ? nt : bt) * brec;
+            xl = (more && lane < W) ? rn[lane * 32] : 0ull;
+            __syncwarp();
+            const ulonglong2 *pc = reinterpret_cast<const ulonglong2 *>(p.trace + bt * brec) + lane;
+            const ulonglong2 *pn = reinterpret_cast<const ulonglong2 *>(rn) + lane;
+            uint32_t myvw = 0;
+#pragma unroll 1
+            for (uint32_t q0 = 0; q0 < npair; q0 += 4) {
+#pragma unroll
+                for (uint32_t u = 0; u < 4; ++u) {
+                    const uint32_t q = q0 + u, g = q + 3;
+                    // streaming loads: every record is read once
+                    r[(u + 3) & 3] = g < npair ? __ldcs(pc + g * 32)
+                                               : (more ? __ldcs(pn + (g - npair) * 32) : z);
+                    pair_step<kSmemTable>(L, r[u], ldp[2 * q + half], q, lane, sv, svs, acc,
+                                          myvw);
+                }
+            }
+            if (lane < W) p.bitmap[(bt * brec >> 5) + lane] = myvw;
+            bt = nt;
+            sel ^= 1;
+        }
+    }
+    // the trace's last, partial batch (if this warp has it)
+    for (; bt < b1; bt += nwarps) {
         const uint64_t r0 = bt * brec;
         const uint64_t nb = min(brec, p.n_rec - r0);
         const uint64_t *recs = p.trace + r0;
@@ -404,7 +469,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         __syncwarp();
         uint32_t *bm = p.bitmap + (r0 >> 5);
         if (nb == brec)
-            batch_words<kSmemTable, true>(L, recs, nb, W, lane, mine, bm, sv, svs, acc);
+            batch_pairs<kSmemTable>(L, recs, W, lane, mine, bm, sv, svs, acc);
         else
             batch_words<kSmemTable, false>(L, recs, nb, W, lane, mine, bm, sv, svs, acc);
         __syncwarp();
@@ -540,7 +605,7 @@ static size_t plan_batched(uint32_t n, int device, bool *smem_table) {
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (optin <= 0) optin = 227 * 1024;
     const uint32_t nvw = (n + 31) / 32;
-    const size_t fixed = sizeof(Lead) * 32 * (kValThreads / 32) + 32 + ((n + 15) & ~15u) +
+    const size_t fixed = sizeof(Lead) * 64 * (kValThreads / 32) + 32 + ((n + 15) & ~15u) +
                          8ull * nvw;
     const size_t tab = 16ull * n;
     *smem_table = fixed + tab <= (size_t)optin;

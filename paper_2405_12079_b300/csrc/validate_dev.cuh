@@ -75,7 +75,9 @@ struct Acc {
 // word, every lane checks its record against that interval with one
 // unsigned compare (broadcast reads), lanes that miss run their own
 // search, and the batch's W bitmap words leave in one coalesced store.
-// Records stream straight from HBM into registers, four words ahead.
+// batch_words takes one word per step (records four words ahead) and
+// serves the trace's last, partial batch; full batches take two words per
+// step (batch_pairs, or the validation kernel's cross-batch stream).
 constexpr uint32_t kBatch = 1024;   // records of a full 32-word batch
 
 struct Lead {
@@ -165,6 +167,113 @@ __device__ __forceinline__ void batch_words(const Look &L, const uint64_t *recs,
         for (uint32_t u = 0; u < 4; ++u) r[u] = n[u];
     }
     if (lane < W && (kFull || lane * 32 < nb)) bm[lane] = myvw;
+}
+
+// Bits 0..15 of x to the even bit positions 0, 2, .., 30.
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// General path of one record of a pair (a lane's element e): interval of
+// the word's leader, else the lane's own search; victims marked here.
+template <bool kSmemTable>
+__device__ __forceinline__ bool pair_record(const Look &L, uint64_t rec, const Lead &ld,
+                                            uint32_t *sv, uint32_t *svs, bool &hit,
+                                            bool &bad) {
+    const uint64_t a = rec & ~PHOS_REC_STORE;
+    const uint32_t st = (uint32_t)(rec >> 63);
+    hit = (a - ld.b) < ld.l;
+    int bi = ld.i;
+    uint32_t pm = ld.pm;
+    bad = false;
+    if (!hit) {
+        bad = a > PHOS_REC_ADDR_MASK;
+        if (!bad) {
+            const int ii = L.lane_search(a);
+            if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
+                hit = true;
+                bi = ii;
+                pm = L.perm[ii];
+            }
+        }
+    }
+    const bool viol = !(hit && ((pm >> st) & 1u));
+    if (viol && hit) {
+        atomicOr(&sv[bi >> 5], 1u << (bi & 31));
+        if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
+    }
+    return viol;
+}
+
+// One pair of a full batch (see batch_pairs): x = this lane's two records,
+// ld = the leader of its word, q = the pair's index in the batch.
+template <bool kSmemTable>
+__device__ __forceinline__ void pair_step(const Look &L, ulonglong2 x, const Lead &ld,
+                                          uint32_t q, uint32_t lane, uint32_t *sv,
+                                          uint32_t *svs, Acc &acc, uint32_t &myvw) {
+    const uint64_t x0 = x.x, x1 = x.y;
+    const uint64_t a0 = x0 & ~PHOS_REC_STORE, a1 = x1 & ~PHOS_REC_STORE;
+    const bool ok0 = (a0 - ld.b) < ld.l && ((ld.pm >> (uint32_t)(x0 >> 63)) & 1u);
+    const bool ok1 = (a1 - ld.b) < ld.l && ((ld.pm >> (uint32_t)(x1 >> 63)) & 1u);
+    if (__ballot_sync(0xffffffffu, !(ok0 && ok1))) {
+        bool h0, h1, bad0, bad1;
+        const bool v0 = pair_record<kSmemTable>(L, x0, ld, sv, svs, h0, bad0);
+        const bool v1 = pair_record<kSmemTable>(L, x1, ld, sv, svs, h1, bad1);
+        const uint32_t b0 = __ballot_sync(0xffffffffu, v0);
+        const uint32_t b1 = __ballot_sync(0xffffffffu, v1);
+        const uint32_t s0 = __ballot_sync(0xffffffffu, v0 && (x0 >> 63));
+        const uint32_t s1 = __ballot_sync(0xffffffffu, v1 && (x1 >> 63));
+        const uint32_t u0 = __ballot_sync(0xffffffffu, !h0);
+        const uint32_t u1 = __ballot_sync(0xffffffffu, !h1);
+        if (lane == 0) {
+            acc.c0 += __popc(b0) + __popc(b1);
+            acc.c1 += __popc(s0) + __popc(s1);
+            acc.c2 += __popc(u0) + __popc(u1);
+        }
+        acc.bad |= bad0 || bad1;
+        const uint32_t lo = spread16(b0) | (spread16(b1) << 1);
+        const uint32_t hi = spread16(b0 >> 16) | (spread16(b1 >> 16) << 1);
+        myvw = lane == 2 * q ? lo : (lane == 2 * q + 1 ? hi : myvw);
+    }
+}
+
+// A full batch two bitmap words at a time: lane l loads records 2l and
+// 2l+1 of the pair with one 16-byte load, so lanes 0-15 cover the first
+// word and lanes 16-31 the second.  When every record of the pair lies in
+// its word's leader interval and the leader's permission admits it (the
+// common case), the pair costs one ballot; otherwise the general path
+// classifies each record, and the two words' bits are put back in record
+// order (record k of a word is element k & 1 of lane k >> 1).  Pairs are
+// loaded three ahead.  recs: 16-byte aligned, 32 * W records, W even.
+template <bool kSmemTable>
+__device__ __forceinline__ void batch_pairs(const Look &L, const uint64_t *recs, uint32_t W,
+                                            uint32_t lane, const Lead *lead, uint32_t *bm,
+                                            uint32_t *sv, uint32_t *svs, Acc &acc) {
+    uint32_t myvw = 0;
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(recs) + lane;
+    const uint32_t npair = W >> 1;
+    // ring of four pairs: pair q sits in slot q % 4, pair q + 3 is loaded
+    // into the slot pair q - 1 left
+    ulonglong2 r[4];
+#pragma unroll
+    for (uint32_t u = 0; u < 3; ++u) r[u] = u < npair ? p[u * 32] : make_ulonglong2(0, 0);
+    const uint32_t half = lane >> 4;
+#pragma unroll 1
+    for (uint32_t q0 = 0; q0 < npair; q0 += 4) {
+#pragma unroll
+        for (uint32_t u = 0; u < 4; ++u) {
+            const uint32_t q = q0 + u;
+            if (q >= npair) break;
+            r[(u + 3) & 3] = q + 3 < npair ? p[(q + 3) * 32] : make_ulonglong2(0, 0);
+            pair_step<kSmemTable>(L, r[u], lead[2 * q + half], q, lane, sv, svs, acc, myvw);
+        }
+    }
+    if (lane < W) bm[lane] = myvw;
 }
 
 }  // namespace phos
