@@ -837,10 +837,11 @@ def run_restore(args, rank, world):
         torch.cuda.synchronize()
         return a.elapsed_time(m), a.elapsed_time(b), dig.clone()
 
-    def concurrent():
+    def concurrent(rounds):
         phos.harness_fill(arena.data_ptr(), lay.arena_bytes, 9, s)
         torch.cuda.synchronize()
-        r = phos.Restore(dp.table, image.data_ptr(), image.numel(), chunk, 4, None, s)
+        r = phos.Restore(dp.table, image.data_ptr(), image.numel(), chunk, 4, None, s,
+                         runner.DeviceProcess._flags(rounds))
         evs = []
         a = torch.cuda.Event(enable_timing=True)
         a.record()
@@ -860,10 +861,11 @@ def run_restore(args, rank, world):
             mis = r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1
             if mis:
-                for j in range(k):
-                    dp.run_kernel(j)
                 break
         r.finish()
+        if r.stats()["misspec_round"] >= 0:     # rolled back: replay what ran
+            for j in range(k):
+                dp.run_kernel(j)
         for j in range(k, K):
             dp.run_kernel(j)
         b = torch.cuda.Event(enable_timing=True)
@@ -879,10 +881,11 @@ def run_restore(args, rank, world):
         return total, first_ms, stalls, st, k, dig.clone()
 
     stw_restore_ms, stw_total_ms, dig_stw = stw()
+    lock = concurrent("sync")
     clk = Clocks(dev)
     clk.start()
     l0 = phos.launch_count()
-    total, first_ms, stalls, st, during, dig_cc = concurrent()
+    total, first_ms, stalls, st, during, dig_cc = concurrent(args.rounds)
     launches = phos.launch_count() - l0
     clocks = clk.stop()
     line = {"metric": METRIC, "value": dp.image_bytes / (total * 1e6), "unit": "GB/s",
@@ -891,7 +894,7 @@ def run_restore(args, rank, world):
             "data": "synthetic",
             "config": {"workload": RESTORE % (dp.image_bytes / 1e9), "image_bytes": dp.image_bytes,
                        "buffers": lay.n, "kernels": len(dp.kernels), "quota": quota,
-                       "chunk": chunk},
+                       "chunk": chunk, "rounds": args.rounds},
             "concurrent": {"total_ms": total, "first_kernel_ms": first_ms,
                            "stall_p50_ms": float(np.percentile(stalls, 50)),
                            "stall_p99_ms": float(np.percentile(stalls, 99)),
@@ -901,9 +904,13 @@ def run_restore(args, rank, world):
                            "misspec_round": st["misspec_round"]},
             "stop_the_world": {"restore_ms": stw_restore_ms, "total_ms": stw_total_ms,
                                "first_kernel_ms": stw_restore_ms},
+            "lockstep": {"total_ms": lock[0], "first_kernel_ms": lock[1],
+                         "stall_p50_ms": float(np.percentile(lock[2], 50)),
+                         "stall_p99_ms": float(np.percentile(lock[2], 99))},
+            "total_speedup_vs_stop_the_world": stw_total_ms / total,
             "first_kernel_speedup": stw_restore_ms / max(first_ms, 1e-6),
             "verified": {"final_memory_equals_stw_restore_plus_replay":
-                         bool(torch.equal(dig_stw, dig_cc))},
+                         bool(torch.equal(dig_stw, dig_cc)) and bool(torch.equal(dig_stw, lock[5]))},
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -513,7 +513,19 @@ phos_status phos_ckpt_end(phos_ckpt_t *c);
 
 typedef struct {
     uint32_t access_bytes;
-    uint32_t reserved;
+    uint32_t flags;          /* PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT, as
+                                for checkpoints: no wait per kernel (the
+                                mis-speculation rule runs on the device and
+                                the rollback happens when the host learns of
+                                it, at the latest at finish; the caller then
+                                replays every kernel it ran); the bulk
+                                restore on a stream of its own, a kernel
+                                waiting for the copier's pieces of the
+                                buffers it is speculated to access.  With
+                                the copier on its own stream, a buffer
+                                counts as restored for the rule once it is
+                                present and the caller's stream has waited
+                                for its last piece.                          */
     uint64_t chunk;          /* multiple of 256                              */
     const void *image;       /* checkpoint image (pinned host or device)     */
     uint64_t image_bytes;
@@ -545,7 +557,9 @@ phos_status phos_restore_before_kernel(phos_restore_t *r, const uint8_t *perm);
  * before the kernel restores every buffer stop-the-world from the image
  * and sets *misspec = 1: the caller replays its kernels from the first
  * (Sec. 6 "roll back ... and perform a stop-the-world restore").
- * Synchronises. */
+ * Synchronises (PHOS_CKPT_NO_SYNC: enqueues; *misspec = 1 only once the
+ * host has seen the device's record; stats.misspec_round >= 0 after
+ * finish says a rollback happened). */
 phos_status phos_restore_after_kernel(phos_restore_t *r, const uint64_t *d_trace,
                                       uint64_t n_rec, int *misspec);
 phos_status phos_restore_finish(phos_restore_t *r);

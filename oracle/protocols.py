@@ -368,11 +368,22 @@ def iterative_recopy(proc, kernels, chunk, quota, max_passes, stop_bytes):
                   kernels_run=k, stats=stats)
 
 
-def concurrent_restore(proc, image, kernels, chunk, quota):
+def concurrent_restore(proc, image, kernels, chunk, quota, copier_stream=False):
     """Section 6 soft on-demand concurrent restore, then the rest of the
-    kernels.  proc.mem holds whatever was there before (not restored)."""
+    kernels.  proc.mem holds whatever was there before (not restored).
+
+    copier_stream: the background copier's pieces run on a stream of their
+    own.  A piece issued in round r lands before a later kernel only if
+    that kernel waited for it, and a kernel waits for the copier's latest
+    piece of each buffer it is speculated to access (all pieces up to that
+    round are then in place, since the copier's pieces land in order).  A
+    buffer counts as restored for the mis-speculation rule once it is
+    present and its last copier piece is at or below the latest round
+    waited for; bytes and the final memory are the same either way."""
     n = proc.n
     present = [False] * n
+    last = [-1] * n                       # round of the copier's last piece of buffer i
+    waited = -1
     cp = Copier(n, proc.size, chunk)
     ondemand = []                         # (k, buf, off, len)
     misspec = None
@@ -382,20 +393,25 @@ def concurrent_restore(proc, image, kernels, chunk, quota):
         io = int(proc.img_off[i]) + off
         proc.buf(i)[off:off + ln] = image[io:io + ln]
 
+    k = 0
+
     def move(i, off, ln):
         fetch(i, off, ln)
         stats["copier_bytes"] += ln
+        last[i] = k
         if off + ln == cp.size[i]:
             present[i] = True
         return False
 
-    k = 0
     while k < len(kernels):
         cp.advance(quota, move, k, skip=lambda i: present[i])
         if all(present):
             break
         kern = kernels[k]
         perm = proc.speculate(kern)
+        if copier_stream:
+            for i in np.nonzero(perm)[0]:
+                waited = max(waited, last[int(i)])
         for i in np.nonzero(perm)[0]:
             i = int(i)
             if not present[i]:
@@ -406,7 +422,7 @@ def concurrent_restore(proc, image, kernels, chunk, quota):
                 cp.copied[i] = cp.size[i]
                 cp.state[i] = DONE
                 present[i] = True
-        before = list(present)
+        before = [present[i] and (not copier_stream or last[i] <= waited) for i in range(n)]
         proc.run_kernel(k, kern)
         res = proc.validate(perm, kern)
         k += 1

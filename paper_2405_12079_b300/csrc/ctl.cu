@@ -74,9 +74,11 @@ struct FirstFit {
 };
 
 // One kernel's validation outcome applied on the device (no-sync sessions).
-// victim_st: the validation's store-victim bitmap; flags[i]: recopy, the
-// buffer was in flight or done when the kernel ran (touched); CoW, it was
-// done or shadowed (safe).  acc: u64[8] device words, [0..2] the
+// victim_st: the validation's store-victim bitmap (restore: its victim
+// bitmap of any access); flags[i]: recopy, the buffer was in flight or done
+// when the kernel ran (touched); CoW, it was done or shadowed (safe);
+// restore, it was restored (present and landed).  cow = 1 for the
+// mis-speculation rule of CoW and restore.  acc: u64[8] device words, [0..2] the
 // validation's counts, [3] running violation total, [4] first mis-speculated
 // round (-1 = none).  One CTA.
 __global__ void k_rule(const uint32_t *victim_st, const uint8_t *flags, uint32_t n, int cow,
@@ -400,7 +402,9 @@ struct Session {
     }
 
     // Validate and apply the rule on the device; returns without waiting.
-    phos_status validate_nosync(const uint64_t *d_trace, uint64_t n_rec, bool cow) {
+    // rule: 0 recopy (dirty marks), 1 CoW (store victims not safe), 2
+    // restore (victims of any access not restored).
+    phos_status validate_nosync(const uint64_t *d_trace, uint64_t n_rec, int rule) {
         // growth synchronises: this round's slot is uploaded by then and
         // later uploads into its device copy are stream-ordered after the
         // validation below
@@ -410,8 +414,8 @@ struct Session {
         phos_status r = phos_validate(t, d_up + slot, d_trace, n_rec, w, d_bitmap, d_acc, d_vic,
                                       d_vic + nvw, nullptr, 0, d_status, s);
         if (r) return r;
-        k_rule<<<1, 256, 0, s>>>(d_vic + nvw, d_up + slot + n, n, cow ? 1 : 0,
-                                 (int64_t)round - 1, d_dirty, d_acc, d_flag);
+        k_rule<<<1, 256, 0, s>>>(rule == 2 ? d_vic : d_vic + nvw, d_up + slot + n, n,
+                                 rule ? 1 : 0, (int64_t)round - 1, d_dirty, d_acc, d_flag);
         PHOS_CUDA(cudaGetLastError());
         count_launch();
         validated += n_rec;
@@ -741,7 +745,7 @@ extern "C" phos_status phos_ckpt_after_kernel(phos_ckpt_t *c, const uint64_t *d_
     const uint64_t k = S.round++;
     if (misspec) *misspec = 0;
     if (S.nosync) {
-        phos_status r = S.validate_nosync(d_trace, n_rec, c->mode == PHOS_CKPT_COW);
+        phos_status r = S.validate_nosync(d_trace, n_rec, c->mode == PHOS_CKPT_COW ? 1 : 0);
         if (r) return r;
         if (c->mode == PHOS_CKPT_COW && S.flag() >= 0) {
             c->misspec = S.flag();
@@ -912,6 +916,7 @@ struct phos_restore {
     uint64_t copier_bytes = 0, ondemand_bytes = 0;
     int64_t misspec = -1;
     bool in_kernel = false;
+    uint64_t waited = 0;     // concurrent: latest copier batch the caller's stream waited for
 
     bool all_present() const {
         for (uint8_t p : present)
@@ -929,8 +934,12 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
     if (!d->image || d->image_bytes < t->image_bytes)
         return fail(PHOS_EINVAL, "restore_begin: image smaller than %llu bytes",
                     (unsigned long long)t->image_bytes);
+    if (d->flags & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT))
+        return fail(PHOS_EINVAL, "restore_begin: flags %#x", d->flags);
     phos_restore *r = new phos_restore();
     phos_status e = r->ss.init(t, static_cast<cudaStream_t>(stream), d->access_bytes, d->chunk);
+    if (!e && (d->flags & PHOS_CKPT_CONCURRENT)) e = r->ss.init_concurrent();
+    if (!e && (d->flags & PHOS_CKPT_NO_SYNC) && !r->ss.nosync) e = r->ss.init_nosync();
     if (e) {
         delete r;
         return e;
@@ -956,6 +965,11 @@ static phos_status restore_advance(phos_restore *R, uint64_t quota) {
     Session &S = R->ss;
     const phos_table *t = S.t;
     std::vector<phos_copy_t> v;
+    const uint64_t b = S.batch + 1;
+    if (S.cs) {
+        PHOS_CUDA(cudaEventRecord(S.app_ev, S.s));
+        PHOS_CUDA(cudaStreamWaitEvent(S.cs, S.app_ev, 0));
+    }
     uint64_t moved = S.advance(
         quota,
         [&](uint32_t i, uint64_t off, uint64_t len) {
@@ -970,10 +984,41 @@ static phos_status restore_advance(phos_restore *R, uint64_t quota) {
                 if (R->d_present) d.flags |= PHOS_COPY_MARK_PRESENT;
             }
             v.push_back(d);
+            if (S.cs) S.last_batch[i] = b;
             return false;
         },
         [&](uint32_t i) { return R->present[i] != 0; });
     R->copier_bytes += moved;
+    phos_status r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present, true);
+    if (r) return r;
+    if (S.cs && !v.empty()) {
+        S.batch = b;
+        PHOS_CUDA(cudaEventRecord(S.bev[b % Session::kRing], S.cs));
+    }
+    return PHOS_OK;
+}
+
+// Mis-speculation (Sec. 6): roll back to the checkpoint's state, every
+// buffer from the image, stop-the-world.  The caller replays the kernels.
+static phos_status restore_rollback(phos_restore *R, int64_t k) {
+    Session &S = R->ss;
+    R->misspec = k;
+    // concurrent: no copier piece may land after the rollback's bytes
+    phos_status r = S.cs ? S.app_wait(S.batch) : PHOS_OK;
+    if (r) return r;
+    std::vector<phos_copy_t> v;
+    for (uint32_t j = 0; j < S.n; ++j) {
+        phos_copy_t d;
+        d.src_off = S.t->img_off[j];
+        d.dst_off = 0;
+        d.len = S.t->size[j];
+        d.buf = j;
+        d.flags = PHOS_COPY_IMAGE_TO_LIVE | (R->d_present ? PHOS_COPY_MARK_PRESENT : 0);
+        v.push_back(d);
+        R->present[j] = 1;
+        S.state[j] = kDone;
+        S.copied[j] = S.t->size[j];
+    }
     return S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
 }
 
@@ -981,6 +1026,10 @@ extern "C" phos_status phos_restore_advance(phos_restore_t *R, uint64_t quota, i
     if (!R) return fail(PHOS_EINVAL, "restore_advance: NULL session");
     if (R->in_kernel) return fail(PHOS_EINVAL, "restore_advance: inside a kernel round");
     phos_status r = PHOS_OK;
+    if (R->ss.nosync && R->misspec < 0 && R->ss.flag() >= 0) {
+        r = restore_rollback(R, R->ss.flag());  // the device saw it
+        if (r) return r;
+    }
     if (!R->all_present()) r = restore_advance(R, quota);
     if (done) *done = R->all_present() ? 1 : 0;
     return r;
@@ -993,6 +1042,18 @@ extern "C" phos_status phos_restore_before_kernel(phos_restore_t *R, const uint8
     const phos_table *t = S.t;
     phos_status r = S.stage_perm(perm);
     if (r) return r;
+    if (S.cs) {
+        // the kernel starts after the copier's pieces of every buffer it is
+        // speculated to access (and so after all earlier pieces)
+        uint64_t need = 0;
+        for (uint32_t i = 0; i < S.n; ++i)
+            if (perm[i]) need = std::max(need, S.last_batch[i]);
+        if (need > R->waited) {
+            r = S.app_wait(need);
+            if (r) return r;
+            R->waited = need;
+        }
+    }
     std::vector<phos_copy_t> v;
     for (uint32_t i = 0; i < S.n; ++i) {
         if (!perm[i] || R->present[i]) continue;
@@ -1010,9 +1071,12 @@ extern "C" phos_status phos_restore_before_kernel(phos_restore_t *R, const uint8
         S.state[i] = kDone;
         R->present[i] = 1;
     }
-    R->before = R->present;
+    // restored before the kernel: present, and (concurrent) landed
+    for (uint32_t i = 0; i < S.n; ++i)
+        R->before[i] = R->present[i] && (!S.cs || S.last_batch[i] <= R->waited);
     r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
     if (r) return r;
+    if (S.nosync && (r = S.upload_slot(R->before))) return r;
     R->in_kernel = true;
     return PHOS_OK;
 }
@@ -1025,27 +1089,22 @@ extern "C" phos_status phos_restore_after_kernel(phos_restore_t *R, const uint64
     R->in_kernel = false;
     const uint64_t k = S.round++;
     if (misspec) *misspec = 0;
+    if (S.nosync) {
+        phos_status r = S.validate_nosync(d_trace, n_rec, 2);
+        if (r) return r;
+        if (R->misspec < 0 && S.flag() >= 0) {
+            r = restore_rollback(R, S.flag());
+            if (r) return r;
+            if (misspec) *misspec = 1;
+        }
+        return PHOS_OK;
+    }
     phos_status r = S.validate_sync(d_trace, n_rec);
     if (r) return r;
     if (S.h_count[0] == S.h_count[2]) return PHOS_OK;  // only unmapped accesses
     for (uint32_t i = 0; i < S.n; ++i) {
         if (S.victim_bit(false, i) && !R->before[i]) {
-            // roll back: every buffer from the image, stop-the-world
-            R->misspec = (int64_t)k;
-            std::vector<phos_copy_t> v;
-            for (uint32_t j = 0; j < S.n; ++j) {
-                phos_copy_t d;
-                d.src_off = S.t->img_off[j];
-                d.dst_off = 0;
-                d.len = S.t->size[j];
-                d.buf = j;
-                d.flags = PHOS_COPY_IMAGE_TO_LIVE | (R->d_present ? PHOS_COPY_MARK_PRESENT : 0);
-                v.push_back(d);
-                R->present[j] = 1;
-                S.state[j] = kDone;
-                S.copied[j] = S.t->size[j];
-            }
-            r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
+            r = restore_rollback(R, (int64_t)k);
             if (r) return r;
             r = S.sync();
             if (r) return r;
@@ -1059,6 +1118,12 @@ extern "C" phos_status phos_restore_after_kernel(phos_restore_t *R, const uint64
 extern "C" phos_status phos_restore_finish(phos_restore_t *R) {
     if (!R) return fail(PHOS_EINVAL, "restore_finish: NULL session");
     if (R->in_kernel) return fail(PHOS_EINVAL, "restore_finish: inside a kernel round");
+    if (R->ss.nosync) {
+        phos_status r = R->ss.collect(nullptr);
+        if (r) return r;
+        if (R->misspec < 0 && R->ss.flag() >= 0 && (r = restore_rollback(R, R->ss.flag())))
+            return r;
+    }
     if (!R->all_present()) {
         phos_status r = restore_advance(R, ~0ull >> 2);
         if (r) return r;

@@ -141,7 +141,7 @@ class CkptStats(_c.Structure):
 
 
 class RestoreDesc(_c.Structure):
-    _fields_ = [("access_bytes", _u32), ("reserved", _u32), ("chunk", _u64), ("image", _vp),
+    _fields_ = [("access_bytes", _u32), ("flags", _u32), ("chunk", _u64), ("image", _vp),
                 ("image_bytes", _u64), ("d_present", _vp)]
 
 
@@ -399,8 +399,10 @@ class Restore:
     """One concurrent restore session (phos_restore_*)."""
 
     def __init__(self, table, image, image_bytes, chunk, access_bytes=4, d_present=None,
-                 stream=None):
-        d = RestoreDesc(access_bytes, 0, chunk, image, image_bytes, d_present)
+                 stream=None, flags=0):
+        """flags: CKPT_NO_SYNC or CKPT_CONCURRENT (the same bits as for
+        checkpoints)."""
+        d = RestoreDesc(access_bytes, flags, chunk, image, image_bytes, d_present)
         h = _vp()
         check(lib().phos_restore_begin(table.handle, _c.byref(d), stream, _c.byref(h)),
               "restore_begin")

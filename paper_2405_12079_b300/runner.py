@@ -124,11 +124,12 @@ class DeviceProcess:
         d = c.log(2)[:, 0].astype(np.int64)
         return int(self.layout.size[d].sum()) if len(d) else 0
 
-    def run_restore(self, image, quota, chunk, d_present=None):
+    def run_restore(self, image, quota, chunk, d_present=None, rounds="sync"):
         """Concurrent restore followed by the rest of the kernels."""
         s = self.stream()
         r = phos.Restore(self.table, image.data_ptr(), image.numel(), chunk, 4,
-                         d_present.data_ptr() if d_present is not None else None, s)
+                         d_present.data_ptr() if d_present is not None else None, s,
+                         self._flags(rounds))
         k = 0
         K = len(self.kernels)
         while k < K:
@@ -140,10 +141,11 @@ class DeviceProcess:
             misspec = r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1
             if misspec:
-                for j in range(k):          # roll back happened: replay
-                    self.run_kernel(j)
                 break
         r.finish()
+        if r.stats()["misspec_round"] >= 0:  # rolled back: replay what ran
+            for j in range(k):
+                self.run_kernel(j)
         during = k
         for j in range(k, K):
             self.run_kernel(j)

@@ -215,6 +215,67 @@ def test_restore_misspeculation_rolls_back():
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("seed,chunk,quota", [(60, 4096, 8192), (61, 256, 1024)])
+def test_restore_copier_stream_without_strays_is_the_same(seed, chunk, quota):
+    """With every access speculated, a copier on its own stream changes no
+    decision: the same on-demand list, copier pieces and final memory."""
+    a, got_a, ref = _restore_pair(seed, chunk=chunk, quota=quota)
+    rng, lay, proc = make_proc(seed)
+    image = P.stw_checkpoint(proc)
+    ks = seq(rng, lay, 40)
+    cur = P.Process(VA0, lay.off, lay.size, np.full(lay.arena_bytes, 0xA5, np.uint8), seed)
+    b = P.concurrent_restore(cur, image, ks, chunk, quota, copier_stream=True)
+    assert b.misspec is None and a.misspec is None
+    assert b.ondemand == a.ondemand and b.copier_log == a.copier_log
+    mask = np.zeros(lay.arena_bytes, bool)
+    for o, sz in zip(lay.off, lay.size):
+        mask[int(o):int(o) + int(sz)] = True
+    assert np.array_equal(cur.mem[mask], ref)
+
+
+def _stray_restore(copier_stream, need_k1):
+    """8 buffers of 8 KiB, one buffer per copier round: round 0 restores
+    buffer 0, round 1 buffer 1.  K0 needs buffer 5; K1 needs need_k1 and
+    makes an unspeculated access to buffer 0."""
+    sizes = np.full(8, 8192, np.uint64)
+
+    def ks(rng, lay):
+        k1 = kernel(rng, lay, [need_k1], [need_k1], strays=[(5, 0)])
+        return [kernel(rng, lay, [5], [5]), k1, kernel(rng, lay, [6], [6])]
+    rng, lay, proc = make_proc(73, sizes=sizes)
+    image = P.stw_checkpoint(proc)
+    kk = ks(rng, lay)
+    ref = P.Process(VA0, lay.off, lay.size, np.zeros(lay.arena_bytes, np.uint8), 73)
+    P.stw_restore(ref, image)
+    for j, k in enumerate(kk):
+        ref.run_kernel(j, k)
+    cur = P.Process(VA0, lay.off, lay.size, np.full(lay.arena_bytes, 0xA5, np.uint8), 73)
+    res = P.concurrent_restore(cur, image, kk, 4096, 8192, copier_stream=copier_stream)
+    mask = np.zeros(lay.arena_bytes, bool)
+    for o, sz in zip(lay.off, lay.size):
+        mask[int(o):int(o) + int(sz)] = True
+    return res, np.array_equal(cur.mem[mask], ref.mem[mask])
+
+
+def test_restore_copier_stream_unwaited_buffer_is_not_restored():
+    """Buffer 0 is present (copied in round 0) but no kernel has waited for
+    the copier yet: an unspeculated access to it in K1 is a mis-speculation
+    with the copier on its own stream and not in lockstep."""
+    lock, ok_lock = _stray_restore(False, 3)
+    stream, ok_stream = _stray_restore(True, 3)
+    assert lock.misspec is None and stream.misspec == 1
+    assert ok_lock and ok_stream
+
+
+def test_restore_copier_stream_wait_covers_earlier_pieces():
+    """K1 needs buffer 1, whose last piece is from round 1: waiting for it
+    also lands buffer 0's round-0 pieces, so the access to buffer 0 is fine."""
+    lock, ok_lock = _stray_restore(False, 1)
+    stream, ok_stream = _stray_restore(True, 1)
+    assert lock.misspec is None and stream.misspec is None
+    assert ok_lock and ok_stream
+
+
 def test_restore_planted_mistake_is_caught(monkeypatch):
     """An oracle that skips on-demand copies reads stale data, and the
     read-dependent mutator makes the final memory differ."""
