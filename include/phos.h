@@ -132,6 +132,22 @@ phos_status phos_speculate(const phos_table_t *t, const void *const *args,
                            const uint32_t *arg_size, const uint8_t *kind,
                            uint32_t nargs, uint8_t *perm_out);
 
+/* The same speculation on the device, for many launches at once (the
+ * batched form: a queue of launches of one process image).  The caller
+ * flattens the arguments into 8-byte words: a pointer argument is one word
+ * (its first 8 bytes, zero-extended), a struct one word per full 8-byte
+ * chunk, scalars may be left out.  d_words: device u64[total words];
+ * d_kind: u8 PHOS_ARG_* of the argument each word came from (a kind above
+ * PHOS_ARG_STRUCT sets d_status to PHOS_EINVAL and the word is ignored);
+ * d_launch_off: u64[n_launch + 1], launch l owns words [off[l], off[l+1])
+ * (a decreasing pair sets PHOS_EINVAL and the launch is skipped); d_perm:
+ * device u8[n_launch][n], row l for launch l, OR-accumulated (zero it
+ * first).  d_status may be NULL.  Asynchronous on stream. */
+phos_status phos_speculate_device(const phos_table_t *t, const uint64_t *d_words,
+                                  const uint8_t *d_kind, const uint64_t *d_launch_off,
+                                  uint32_t n_launch, uint8_t *d_perm, uint32_t *d_status,
+                                  phos_stream_t stream);
+
 /* Type-1 APIs (Sec. 4.1, memory moves): a call that reads or writes
  * [addr, addr + len) marks every buffer the range overlaps with perm. */
 phos_status phos_speculate_region(const phos_table_t *t, uint64_t addr, uint64_t len,

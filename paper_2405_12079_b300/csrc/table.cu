@@ -214,6 +214,71 @@ extern "C" phos_status phos_speculate(const phos_table_t *t, const void *const *
     return PHOS_OK;
 }
 
+// Device speculation: one warp per launch.  Lanes look up 32 argument words
+// at a time (binary search over the device table); the hits are then
+// OR-ed into the launch's perm row one lane after another, so no two lanes
+// update a byte at once and no atomics are needed (each row belongs to
+// one warp).
+__global__ void k_speculate(phos::TableDev tab, const uint64_t *words, const uint8_t *kind,
+                            const uint64_t *off, uint32_t n_launch, uint8_t *perm,
+                            uint32_t *status) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t l = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (l >= n_launch) return;
+    const uint64_t j0 = off[l], j1 = off[l + 1];
+    uint8_t *row = perm + l * (uint64_t)tab.n;
+    if (j1 < j0) {
+        if (lane == 0) phos::set_status(status, PHOS_EINVAL);
+        return;
+    }
+    for (uint64_t jb = j0; jb < j1; jb += 32) {
+        const uint64_t j = jb + lane;
+        int hit = -1;
+        uint8_t pm = 0;
+        if (j < j1) {
+            const uint8_t k = kind[j];
+            if (k > PHOS_ARG_STRUCT) phos::set_status(status, PHOS_EINVAL);
+            if (k == PHOS_ARG_CONST_PTR || k == PHOS_ARG_MUT_PTR || k == PHOS_ARG_STRUCT) {
+                const uint64_t v = words[j];
+                uint32_t lo = 0, cnt = tab.n;       // last base <= v
+                while (cnt > 0) {
+                    const uint32_t half = cnt >> 1;
+                    if (tab.base[lo + half] <= v) {
+                        lo += half + 1;
+                        cnt -= half + 1;
+                    } else {
+                        cnt = half;
+                    }
+                }
+                if (lo > 0 && v - tab.base[lo - 1] < tab.size[lo - 1]) {
+                    hit = (int)lo - 1;
+                    pm = k == PHOS_ARG_CONST_PTR ? PHOS_PERM_R : PHOS_PERM_RW;
+                }
+            }
+        }
+        for (uint32_t q = 0; q < 32; ++q) {
+            if (lane == q && hit >= 0) row[hit] |= pm;
+            __syncwarp();
+        }
+    }
+}
+
+extern "C" phos_status phos_speculate_device(const phos_table_t *t, const uint64_t *d_words,
+                                             const uint8_t *d_kind, const uint64_t *d_launch_off,
+                                             uint32_t n_launch, uint8_t *d_perm,
+                                             uint32_t *d_status, phos_stream_t stream) {
+    if (!t || (n_launch && (!d_launch_off || !d_perm)))
+        return fail(PHOS_EINVAL, "speculate_device: NULL argument");
+    if (n_launch == 0 || t->n == 0) return PHOS_OK;
+    const uint32_t warps = 8;
+    const unsigned grid = (unsigned)((n_launch + warps - 1) / warps);
+    k_speculate<<<grid, 32 * warps, 0, static_cast<cudaStream_t>(stream)>>>(
+        t->view, d_words, d_kind, d_launch_off, n_launch, d_perm, d_status);
+    count_launch();
+    PHOS_CUDA(cudaGetLastError());
+    return PHOS_OK;
+}
+
 extern "C" phos_status phos_speculate_region(const phos_table_t *t, uint64_t addr, uint64_t len,
                                              uint8_t perm, uint8_t *perm_out) {
     if (!t || !perm_out) return fail(PHOS_EINVAL, "speculate_region: NULL argument");

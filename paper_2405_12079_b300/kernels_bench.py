@@ -168,9 +168,36 @@ def bench_copy(gb, out):
     out["dma_and_engine_d2h"] = dict(gbs=G / ms / 1e6)
 
 
+def bench_speculate(out, n_launch=20000):
+    """Device speculation of a queue of launches over the 1,000-buffer
+    training table, against the host call per launch."""
+    import time
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(n_kernels=1)
+    lay, rng = cfg["layout"], cfg["rng"]
+    t = phos.Table(lay.base(VA0), lay.size)
+    launches = [wl.make_args(rng, lay, VA0, *wl.pick_sets(rng, lay.n)) for _ in range(n_launch)]
+    words, wk, off = phos.flatten_launch_args(launches)
+    d_w = torch.from_numpy(words.view(np.uint8).copy()).cuda()
+    d_k = torch.from_numpy(wk.copy()).cuda()
+    d_o = torch.from_numpy(off.view(np.uint8).copy()).cuda()
+    d_p = torch.zeros(n_launch * lay.n, dtype=torch.uint8, device="cuda")
+    ms = timeit(lambda: phos.speculate_device(t, d_w.data_ptr(), d_k.data_ptr(), d_o.data_ptr(),
+                                              n_launch, d_p.data_ptr(), None, s))
+    perm = np.zeros(lay.n, np.uint8)
+    t0 = time.perf_counter()
+    for args, kinds in launches[:2000]:
+        perm[:] = 0
+        phos.speculate(t, args, kinds, perm)
+    host_us = 1e6 * (time.perf_counter() - t0) / 2000
+    out["speculate_device"] = dict(launches=n_launch, words=len(words), ms=ms,
+                                   launches_per_s=n_launch / ms * 1e3,
+                                   host_us_per_launch=host_us)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", default="all", choices=["validate", "copy", "all"])
+    ap.add_argument("--kernel", default="all", choices=["validate", "copy", "speculate", "all"])
     ap.add_argument("--traces", type=int, default=160)
     ap.add_argument("--copy-gb", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0, help="validate kernel variant (0 = both)")
@@ -180,6 +207,8 @@ def main():
         bench_validate(a.traces, out, (1, 2) if a.variant == 0 else (a.variant,))
     if a.kernel in ("copy", "all"):
         bench_copy(a.copy_gb, out)
+    if a.kernel in ("speculate", "all"):
+        bench_speculate(out)
     print(json.dumps(out, indent=1))
     sys.stdout.flush()
 

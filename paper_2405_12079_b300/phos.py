@@ -70,6 +70,7 @@ _SIGS = {
     "phos_server_poll": (_i32, [_vp, _u64, _vp]),
     "phos_server_drain": (_i32, [_vp, _u32]),
     "phos_server_stop": (_i32, [_vp]),
+    "phos_speculate_device": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp]),
     "phos_server_app_copy": (_i32, [_vp, _vp, _vp, _u64, _vp]),
     "phos_server_stats": (_i32, [_vp, _vp]),
     "phos_ckpt_begin": (_i32, [_vp, _vp, _vp, _P(_vp)]),
@@ -241,6 +242,33 @@ def speculate(table, args, kinds, perm=None):
     check(lib().phos_speculate(table.handle, argv, asz.ctypes.data, kd.ctypes.data, nargs,
                                out.ctypes.data), "speculate")
     return out[:n] if perm is None else out
+
+
+def flatten_launch_args(launches):
+    """Argument words for phos_speculate_device: launches is a list of
+    (args, kinds) as for speculate().  A pointer argument gives its first 8
+    bytes (zero-extended), a struct each full 8-byte chunk, a scalar
+    nothing.  Returns (u64 words, u8 kinds, u64 offsets[n_launch + 1])."""
+    words, wk, off = [], [], [0]
+    for args, kinds in launches:
+        for a, k in zip(args, kinds):
+            a = bytes(a)
+            if k == ARG_STRUCT:
+                for o in range(0, len(a) - 7, 8):
+                    words.append(int.from_bytes(a[o:o + 8], "little"))
+                    wk.append(k)
+            elif k != ARG_SCALAR:
+                words.append(int.from_bytes(a[:8].ljust(8, b"\0"), "little"))
+                wk.append(k)
+        off.append(len(words))
+    return (np.array(words, np.uint64), np.array(wk, np.uint8), np.array(off, np.uint64))
+
+
+def speculate_device(table, d_words, d_kind, d_off, n_launch, d_perm, d_status=None,
+                     stream=None):
+    """phos_speculate_device with integer device pointers."""
+    return check(lib().phos_speculate_device(table.handle, d_words, d_kind, d_off, n_launch,
+                                             d_perm, d_status, stream), "speculate_device")
 
 
 def speculate_region(table, addr, length, perm_bits, perm):
