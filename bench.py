@@ -723,7 +723,8 @@ def run_serving(args, rank, world):
     torch.cuda.synchronize()
 
     def run(slots):
-        srv = phos.Server(slots, staging.data_ptr(), stg_b, chunk=4 << 20, dma_min=1 << 20)
+        srv = phos.Server(slots, staging.data_ptr(), stg_b, chunk=4 << 20, dma_min=1 << 20,
+                          window=args.server_window << 20)
         tickets = [None] * len(tables)
         errors = []
         t0 = time.monotonic_ns()
@@ -1219,6 +1220,8 @@ def main():
     ap.add_argument("--rounds", default="concurrent", choices=["sync", "nosync", "concurrent"],
                     help="nosync: protocol rounds do not wait for validation (device-side "
                          "rule); concurrent: also the copier on its own stream")
+    ap.add_argument("--server-window", type=int, default=0,
+                    help="serving: host-leg MiB queued per direction (0 = two 64 MiB batches)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (parity / quick runs); 1.0 = the full 40 GB")
     args = ap.parse_args()

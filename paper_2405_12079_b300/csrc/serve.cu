@@ -77,6 +77,7 @@ struct AppCopy {
 using namespace phos;
 
 struct phos_server {
+    static constexpr uint64_t kMaxRun = 64ull << 20;   // largest merged DMA copy
     phos_server_desc_t d{};
     int device = 0;
     cudaStream_t s_snap = nullptr, s_d2h = nullptr, s_h2d = nullptr;
@@ -260,24 +261,45 @@ struct phos_server {
         for (size_t c = 0; c < cand.size(); ++c) {
             if (lists[c].empty()) continue;
             Req &q = *cand[c];
+            const phos_table *t = q.r.table;
             std::vector<phos_copy_t> kern;
-            for (const phos_copy_t &p : lists[c]) {
-                if (d.dma_min && p.len >= d.dma_min) {
-                    const phos_table *t = q.r.table;
-                    const uint8_t *src;
-                    uint8_t *dst;
+            // Runs of pieces that are contiguous on both sides (adjacent
+            // buffers whose sizes are multiples of 256, and for a restore
+            // adjacent in the address space too) move as one DMA copy once
+            // the run reaches dma_min; shorter runs go to the SM kernel
+            // piece by piece.
+            const std::vector<phos_copy_t> &L = lists[c];
+            size_t k = 0;
+            while (k < L.size()) {
+                auto ptrs = [&](const phos_copy_t &p, const uint8_t **src, uint8_t **dst) {
                     if (d2h) {
-                        src = static_cast<const uint8_t *>(d.d_staging) + p.src_off;
-                        dst = static_cast<uint8_t *>(q.r.host) + p.dst_off;
+                        *src = static_cast<const uint8_t *>(d.d_staging) + p.src_off;
+                        *dst = static_cast<uint8_t *>(q.r.host) + p.dst_off;
                     } else {
-                        src = static_cast<const uint8_t *>(q.r.host) + p.src_off;
-                        dst = reinterpret_cast<uint8_t *>(t->base[p.buf] + p.dst_off);
+                        *src = static_cast<const uint8_t *>(q.r.host) + p.src_off;
+                        *dst = reinterpret_cast<uint8_t *>(t->base[p.buf] + p.dst_off);
                     }
-                    cudaError_t ce = cudaMemcpyAsync(dst, src, p.len, cudaMemcpyDefault, s);
+                };
+                const uint8_t *s0;
+                uint8_t *d0;
+                ptrs(L[k], &s0, &d0);
+                uint64_t run = L[k].len;
+                size_t e = k + 1;
+                while (e < L.size() && run < kMaxRun) {
+                    const uint8_t *s1;
+                    uint8_t *d1;
+                    ptrs(L[e], &s1, &d1);
+                    if (s1 != s0 + run || d1 != d0 + run) break;
+                    run += L[e].len;
+                    ++e;
+                }
+                if (d.dma_min && run >= d.dma_min) {
+                    cudaError_t ce = cudaMemcpyAsync(d0, s0, run, cudaMemcpyDefault, s);
                     if (ce != cudaSuccess) q.res.status = PHOS_ECUDA;
                 } else {
-                    kern.push_back(p);
+                    kern.insert(kern.end(), L.begin() + k, L.begin() + e);
                 }
+                k = e;
             }
             phos_status e = launch(d2h ? 1 : 2, s, q.r.table, kern, q.r.host, q.r.host_bytes);
             if (e) q.res.status = e;

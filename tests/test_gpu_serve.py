@@ -21,7 +21,9 @@ def a256(x):
 class World:
     """Disjoint device and host regions, one per request."""
 
-    def __init__(self, seed, n_req=24):
+    def __init__(self, seed, n_req=24, packed=False):
+        """packed: buffer sizes multiples of 256 with no gaps, so pieces of
+        neighbouring buffers are contiguous on both sides and merge."""
         rng = np.random.default_rng(seed)
         self.rng = rng
         self.dev_h = rng.integers(0, 256, 96 << 20, dtype=np.uint8)
@@ -33,7 +35,11 @@ class World:
         for q in range(n_req):
             nb = int(rng.integers(1, 300))
             sizes = wl.sizes_uniform(rng, nb, 1, int(rng.integers(2_000, 60_000)))
-            lay = wl.make_layout(rng, sizes, gap_lo=0, gap_hi=2048)
+            if packed:
+                sizes = (sizes + np.uint64(255)) // np.uint64(256) * np.uint64(256)
+                lay = wl.make_layout(rng, sizes, gap_lo=0, gap_hi=0)
+            else:
+                lay = wl.make_layout(rng, sizes, gap_lo=0, gap_hi=2048)
             off = doff
             doff += lay.arena_bytes + 4096
             t = phos.Table(lay.base(self.dev.data_ptr() + off), lay.size)
@@ -70,9 +76,10 @@ class World:
                           a256(r["img"]))
 
 
+@pytest.mark.parametrize("packed", [False, True], ids=["gaps", "packed"])
 @pytest.mark.parametrize("dma_min", [0, 256 << 10], ids=["sm-copies", "dma"])
-def test_alone_and_mix_give_the_same_bytes(dma_min):
-    w = World(5)
+def test_alone_and_mix_give_the_same_bytes(dma_min, packed):
+    w = World(5, packed=packed)
     exp_dev, exp_host = w.expected()
     cks = [a256(r["img"]) for r in w.reqs if r["kind"] == phos.REQ_CHECKPOINT]
     stg = max(max(cks), sum(cks) // 2)       # smaller than all checkpoints together
