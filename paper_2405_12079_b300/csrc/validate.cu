@@ -433,6 +433,11 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
             }
             const uint64_t *rn = p.trace + (more ? nt : bt) * brec;
             xl = (more && lane < W) ? rn[lane * 32] : 0ull;
+            // the next batch into L2 while this one is worked on (one batch
+            // ahead: two ahead thrashed L2 and measured 25 % slower)
+            if (more && lane == 0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(rn),
+                             "r"((uint32_t)(brec * 8)) : "memory");
             __syncwarp();
             const ulonglong2 *pc = reinterpret_cast<const ulonglong2 *>(p.trace + bt * brec) + lane;
             const ulonglong2 *pn = reinterpret_cast<const ulonglong2 *>(rn) + lane;
