@@ -846,22 +846,28 @@ def run_restore(args, rank, world):
         torch.cuda.synchronize()
         r = phos.Restore(dp.table, image.data_ptr(), image.numel(), chunk, 4, None, s,
                          runner.DeviceProcess._flags(rounds))
+        # stall of kernel k: from the end of kernel k-1 (the session start
+        # for k = 0) to the start of kernel k on the application's stream,
+        # i.e. everything the kernel waited for: copier pieces ahead of it
+        # on the stream (lockstep) or the copier batches it waits for
+        # (concurrent), and its on-demand copies
         evs = []
         a = torch.cuda.Event(enable_timing=True)
         a.record()
+        prev = a
         k, first = 0, None
         K = len(dp.kernels)
         while k < K:
             if r.advance(quota):
                 break
             pk = dp.kernels[k]
-            e0 = torch.cuda.Event(enable_timing=True)
-            e0.record()
             r.before_kernel(pk.speculate(dp.table, dp.perm))
             e1 = torch.cuda.Event(enable_timing=True)
             e1.record()
-            evs.append((e0, e1))
+            evs.append((prev, e1))
             dp.run_kernel(k)
+            prev = torch.cuda.Event(enable_timing=True)
+            prev.record()
             mis = r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1
             if mis:
