@@ -1131,8 +1131,9 @@ ROUNDS = ("per-round overhead of the lockstep protocol: the training-process tab
           "buffers, %.1f GB) with %d short kernels (65,536-record traces); one soft recopy "
           "session (and one soft CoW session, staging image/20) whose copier moves image/2000 per "
           "round in 4 MB pieces; lockstep rounds that wait for each validation, no-sync rounds "
-          "(rule on the device) and the concurrent copier (own stream), against the kernels "
-          "alone")
+          "(rule on the device) and the concurrent copier (own stream), each driven from Python "
+          "and through the library's native round driver, against the kernels alone; value = "
+          "kernel rounds/s of the native concurrent recopy")
 
 
 def run_rounds(args, rank, world):
@@ -1179,6 +1180,25 @@ def run_rounds(args, rank, world):
         return {"rounds": k, "ms_per_round": 1e3 * (t1 - t0) / k, "dirty": st["dirty"],
                 "copier_bytes": st["copier_bytes"]}
 
+    ks = dp.native_kernels()
+
+    def native(rounds, cow=False):
+        """The same session through the library's native round driver: no
+        interpreter between the calls of a round."""
+        mode = (phos.CKPT_COW if cow else phos.CKPT_RECOPY) | runner.DeviceProcess._flags(rounds)
+        c = phos.Checkpoint(dp.table, mode, image.data_ptr(), image.numel(), 4 << 20, 4,
+                            staging.data_ptr() if cow else None, staging.numel() if cow else 0, s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = phos.harness_drive_ckpt(c, dp.table, dp.seed, quota, ks, s)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st = c.stats()
+        c.finish()
+        c.close()
+        return {"rounds": k, "ms_per_round": 1e3 * (t1 - t0) / k, "dirty": st["dirty"],
+                "copier_bytes": st["copier_bytes"]}
+
     def alone():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1194,9 +1214,14 @@ def run_rounds(args, rank, world):
     for r in ("sync", "nosync", "concurrent"):
         res["recopy_" + r] = session(r)
         res["cow_" + r] = session(r, cow=True)
+    for r in ("sync", "concurrent"):
+        native(r)
+        res["native_recopy_" + r] = native(r)
+        res["native_cow_" + r] = native(r, cow=True)
     launches = phos.launch_count() - l0
     assert res["recopy_sync"]["dirty"] == res["recopy_concurrent"]["dirty"]
-    best = res["recopy_concurrent"]
+    assert res["native_recopy_sync"]["dirty"] == res["recopy_sync"]["dirty"]
+    best = res["native_recopy_concurrent"]
     line = {"metric": METRIC, "value": 1e3 / best["ms_per_round"],
             "unit": "kernel rounds/s", "higher_is_better": True, "n_gpus": world, "steps": 1,
             "warmup": 1, "ms_per_step": best["ms_per_round"] * best["rounds"],
@@ -1204,7 +1229,11 @@ def run_rounds(args, rank, world):
             "config": {"workload": ROUNDS % (dp.image_bytes / 1e9, n_k)},
             "arms": res,
             "recopy_speedup_concurrent_vs_sync": res["recopy_sync"]["ms_per_round"] /
-            best["ms_per_round"],
+            res["recopy_concurrent"]["ms_per_round"],
+            "native_recopy_speedup_concurrent_vs_sync":
+                res["native_recopy_sync"]["ms_per_round"] / best["ms_per_round"],
+            "native_recopy_overhead_vs_kernels_alone":
+                best["ms_per_round"] / res["kernels_alone"]["ms_per_round"] - 1.0,
             "cow_speedup_concurrent_vs_sync": res["cow_sync"]["ms_per_round"] /
             res["cow_concurrent"]["ms_per_round"], "gpu_launches": launches}
     if rank == 0:

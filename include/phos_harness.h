@@ -44,6 +44,36 @@ phos_status phos_harness_mutate(const phos_table_t *t, uint64_t seed, uint64_t k
                                 uint32_t nw, const uint64_t *d_strays, uint32_t ns,
                                 phos_stream_t stream);
 
+/* One application kernel of the stand-in, as the native driver below runs
+ * it: its launch arguments (for speculation, phos_speculate's layout), the
+ * mutator's read and write sets and stray stores (phos_harness_mutate's),
+ * and its recorded access trace (device, 16-byte aligned). */
+typedef struct {
+    const void *const *args;
+    const uint32_t *arg_size;
+    const uint8_t *kind;
+    uint32_t nargs;
+    uint32_t nr;
+    const uint32_t *reads;
+    const uint32_t *writes;
+    uint32_t nw;
+    uint32_t ns;
+    const uint64_t *d_strays;
+    const uint64_t *d_trace;
+    uint64_t n_rec;
+} phos_harness_kernel_t;
+
+/* Drive a checkpoint session natively through kernels [0, n) of the stand-in,
+ * one round per kernel in the order the session defines: copier advance by
+ * quota bytes (stop when it reports done), speculation of the kernel's
+ * arguments and before_kernel, the mutator as the kernel (seed, index k),
+ * after_kernel on its trace (stop after a reported mis-speculation).  The
+ * session is not finished.  *kernels_run = rounds run.  Host work per round
+ * is the library's own: no interpreter between the calls. */
+phos_status phos_harness_drive_ckpt(phos_ckpt_t *c, const phos_table_t *t, uint64_t seed,
+                                    uint64_t quota, const phos_harness_kernel_t *ks, uint32_t n,
+                                    phos_stream_t stream, uint32_t *kernels_run);
+
 /* Fill [ptr, ptr + len) (device address) with bytes of sm(key ^ j) words:
  * used to give live memory and arenas a reproducible initial content. */
 phos_status phos_harness_fill(uint64_t ptr, uint64_t len, uint64_t key, phos_stream_t stream);

@@ -264,3 +264,30 @@ extern "C" phos_status phos_harness_fill(uint64_t ptr, uint64_t len, uint64_t ke
         return PHOS_OK;
     });
 }
+
+extern "C" phos_status phos_harness_drive_ckpt(phos_ckpt_t *c, const phos_table_t *t,
+                                               uint64_t seed, uint64_t quota,
+                                               const phos_harness_kernel_t *ks, uint32_t n,
+                                               phos_stream_t stream, uint32_t *kernels_run) {
+    if (!c || !t || (n && !ks)) return fail(PHOS_EINVAL, "harness_drive_ckpt: NULL argument");
+    std::vector<uint8_t> perm(std::max(t->n, 1u));
+    uint32_t k = 0;
+    phos_status r = PHOS_OK;
+    while (k < n) {
+        int done = 0, mis = 0;
+        if ((r = phos_ckpt_advance(c, quota, &done))) break;
+        if (done) break;
+        const phos_harness_kernel_t &K = ks[k];
+        std::fill(perm.begin(), perm.end(), 0);
+        if ((r = phos_speculate(t, K.args, K.arg_size, K.kind, K.nargs, perm.data()))) break;
+        if ((r = phos_ckpt_before_kernel(c, perm.data()))) break;
+        if ((r = phos_harness_mutate(t, seed, k, K.reads, K.nr, K.writes, K.nw, K.d_strays, K.ns,
+                                     stream)))
+            break;
+        if ((r = phos_ckpt_after_kernel(c, K.d_trace, K.n_rec, &mis))) break;
+        ++k;
+        if (mis) break;
+    }
+    if (kernels_run) *kernels_run = k;
+    return r;
+}

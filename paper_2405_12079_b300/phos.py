@@ -58,6 +58,7 @@ _SIGS = {
     "phos_image_offsets": (_i32, [_vp, _vp]),
     "phos_harness_digest": (_i32, [_vp, _vp, _u32, _vp, _vp]),
     "phos_harness_mutate": (_i32, [_vp, _u64, _u64, _vp, _u32, _vp, _u32, _vp, _u32, _vp]),
+    "phos_harness_drive_ckpt": (_i32, [_vp, _vp, _u64, _u64, _vp, _u32, _vp, _P(_u32)]),
     "phos_harness_fill": (_i32, [_u64, _u64, _u64, _vp]),
     "phos_plan_create": (_i32, [_vp, _u32, _P(_vp)]),
     "phos_plan_launch": (_i32, [_vp, _vp]),
@@ -353,6 +354,22 @@ def harness_mutate(table, seed, k, reads, writes, d_strays=None, ns=0, stream=No
     return check(lib().phos_harness_mutate(table.handle, seed & (2**64 - 1), k, _np_ptr(r),
                                            len(r), _np_ptr(w), len(w), d_strays, ns, stream),
                  "harness_mutate")
+
+
+class HarnessKernel(_c.Structure):
+    _fields_ = [("args", _vp), ("arg_size", _vp), ("kind", _vp), ("nargs", _u32),
+                ("nr", _u32), ("reads", _vp), ("writes", _vp), ("nw", _u32), ("ns", _u32),
+                ("d_strays", _vp), ("d_trace", _vp), ("n_rec", _u64)]
+
+
+def harness_drive_ckpt(ckpt, table, seed, quota, kernels, stream=None):
+    """phos_harness_drive_ckpt over an array of HarnessKernel; returns the
+    number of rounds run."""
+    n = _u32()
+    check(lib().phos_harness_drive_ckpt(ckpt.h, table.handle, seed & (2**64 - 1), quota,
+                                        _c.cast(kernels, _vp), len(kernels), stream,
+                                        _c.byref(n)), "harness_drive_ckpt")
+    return int(n.value)
 
 
 def harness_fill(ptr, length, key, stream=None):

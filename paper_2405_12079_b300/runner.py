@@ -67,6 +67,18 @@ class DeviceProcess:
     def stream(self):
         return torch.cuda.current_stream().cuda_stream
 
+    def native_kernels(self):
+        """The kernels as phos_harness_kernel_t entries for the native
+        driver (the PreparedKernel objects keep the memory alive)."""
+        arr = (phos.HarnessKernel * max(len(self.kernels), 1))()
+        for j, pk in enumerate(self.kernels):
+            arr[j] = phos.HarnessKernel(
+                ctypes.cast(pk.argv, ctypes.c_void_p), pk.asz.ctypes.data, pk.kinds.ctypes.data,
+                pk.nargs, len(pk.reads), pk.reads.ctypes.data if len(pk.reads) else None,
+                pk.writes.ctypes.data if len(pk.writes) else None, len(pk.writes), pk.ns,
+                pk.d_strays.data_ptr(), pk.d_trace.data_ptr(), pk.n_rec)
+        return arr
+
     def run_kernel(self, k):
         pk = self.kernels[k]
         phos.harness_mutate(self.table, self.seed, k, pk.reads, pk.writes,
@@ -114,6 +126,22 @@ class DeviceProcess:
             k += 1
             if misspec:
                 break
+        c.finish()
+        out = dict(stats=c.stats(), cow=c.log(0), copier=c.log(1), dirty=c.log(2)[:, 0],
+                   passes=c.log(3), kernels_run=k)
+        c.close()
+        return out
+
+    def run_native(self, mode, image, quota, chunk, staging=None, staging_bytes=0,
+                   rounds="sync"):
+        """The same checkpoint rounds through the library's native driver
+        (phos_harness_drive_ckpt) instead of this module's loop."""
+        s = self.stream()
+        c = phos.Checkpoint(self.table, mode | self._flags(rounds), image.data_ptr(),
+                            image.numel(), chunk, 4,
+                            staging.data_ptr() if staging is not None else None, staging_bytes, s)
+        ks = self.native_kernels()
+        k = phos.harness_drive_ckpt(c, self.table, self.seed, quota, ks, s)
         c.finish()
         out = dict(stats=c.stats(), cow=c.log(0), copier=c.log(1), dirty=c.log(2)[:, 0],
                    passes=c.log(3), kernels_run=k)

@@ -265,3 +265,28 @@ def test_iterative_recopy(div, n_kernels, stray, max_passes, stop, rounds):
     assert got["stats"]["copier_bytes"] == exp.stats["copier_bytes"]
     assert np.array_equal(img.numpy(), exp.image)
     assert w.live_equal(proc)
+
+
+@pytest.mark.parametrize("rounds", ["sync", "concurrent"])
+@pytest.mark.parametrize("mode", ["cow", "recopy"])
+def test_native_driver_equals_oracle(mode, rounds):
+    """The library's native round driver gives the oracle's results too."""
+    w, cfg = training_world(wl.SEED0 + 2, 0.002, 200)
+    quota = a256(w.dp.image_bytes / 100)
+    chunk = 64 * 1024
+    img = torch.zeros(w.dp.image_bytes, dtype=torch.uint8).pin_memory()
+    stg = torch.zeros(4 << 20, dtype=torch.uint8, device="cuda")
+    proc = w.oracle_proc()
+    if mode == "cow":
+        exp = P.cow_checkpoint(proc, w.kernels, 4 << 20, chunk, quota)
+        got = w.dp.run_native(phos.CKPT_COW, img, quota, chunk, stg, 4 << 20, rounds)
+        assert [tuple(int(x) for x in r) for r in got["cow"]] == cow_rows(exp.cow_log)
+    else:
+        exp = P.recopy_checkpoint(proc, w.kernels, chunk, quota)
+        got = w.dp.run_native(phos.CKPT_RECOPY, img, quota, chunk, rounds=rounds)
+        assert got["dirty"].tolist() == exp.dirty
+    torch.cuda.synchronize()
+    assert got["kernels_run"] == exp.kernels_run
+    assert [tuple(int(x) for x in r) for r in got["copier"]] == copier_rows(exp.copier_log)
+    assert np.array_equal(img.numpy(), exp.image)
+    assert w.live_equal(proc)
