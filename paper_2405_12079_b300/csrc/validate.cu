@@ -624,10 +624,20 @@ static uint32_t g_val_ctas = 0;     // 0 auto (one per SM), else the grid size
 // unless that leaves fewer than two batches per warp of the grid; then 16,
 // then 8, so small traces still occupy every warp.
 static uint32_t words_per_batch(uint64_t n_rec, uint64_t ctas) {
+    // the W in {32, 16, 8} whose busiest warp has the fewest words, the
+    // larger W on a tie (fewer leader searches)
     const uint64_t warps = ctas * (kValThreads / 32);
-    uint32_t W = 32;
-    while (W > 8 && (n_rec + 32ull * W - 1) / (32ull * W) < 2 * warps) W /= 2;
-    return W;
+    uint32_t best = 32;
+    uint64_t best_words = ~0ull;
+    for (uint32_t W = 32; W >= 8; W /= 2) {
+        const uint64_t nb = (n_rec + 32ull * W - 1) / (32ull * W);
+        const uint64_t words = (nb + warps - 1) / warps * W;
+        if (words < best_words) {
+            best_words = words;
+            best = W;
+        }
+    }
+    return best;
 }
 
 }  // namespace phos
