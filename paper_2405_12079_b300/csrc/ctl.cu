@@ -8,8 +8,9 @@
 // synchronisations that after_kernel performs anyway to read the victims.
 //
 // No-sync checkpoint sessions (PHOS_CKPT_NO_SYNC) take that round trip out:
-// after_kernel enqueues the validation and a one-CTA rule kernel that
-// applies the protocol's response on the device (recopy: store victims
+// after_kernel enqueues the validation, whose last CTA (or, after the
+// ring variant, a one-CTA rule kernel) applies the protocol's response on
+// the device (recopy: store victims
 // that were in flight or done become dirty; CoW: the first round with a
 // store victim neither done nor shadowed is recorded and published to a
 // mapped host word), and returns at once.  Every host decision of a round
@@ -411,13 +412,25 @@ struct Session {
         phos_status r0 = bitmap_for(n_rec);
         if (r0) return r0;
         const uint32_t nvw = std::max((n + 31) / 32, 1u);
-        phos_status r = phos_validate(t, d_up + slot, d_trace, n_rec, w, d_bitmap, d_acc, d_vic,
-                                      d_vic + nvw, nullptr, 0, d_status, s);
+        // the validation kernel's last CTA applies the rule when it can;
+        // otherwise (ring variant, empty trace) k_rule does
+        ProtoRule pr;
+        pr.flags = d_up + slot + n;
+        pr.dirty = d_dirty;
+        pr.acc = d_acc;
+        pr.h_flag = d_flag;
+        pr.round = (int64_t)round - 1;
+        pr.kind = rule == 0 ? 1u : (rule == 1 ? 2u : 3u);
+        bool fused = false;
+        phos_status r = validate_impl(t, d_up + slot, d_trace, n_rec, w, d_bitmap, d_acc, d_vic,
+                                      d_vic + nvw, nullptr, 0, d_status, s, &pr, &fused);
         if (r) return r;
-        k_rule<<<1, 256, 0, s>>>(rule == 2 ? d_vic : d_vic + nvw, d_up + slot + n, n,
-                                 rule ? 1 : 0, (int64_t)round - 1, d_dirty, d_acc, d_flag);
-        PHOS_CUDA(cudaGetLastError());
-        count_launch();
+        if (!fused) {
+            k_rule<<<1, 256, 0, s>>>(rule == 2 ? d_vic : d_vic + nvw, d_up + slot + n, n,
+                                     rule ? 1 : 0, (int64_t)round - 1, d_dirty, d_acc, d_flag);
+            PHOS_CUDA(cudaGetLastError());
+            count_launch();
+        }
         validated += n_rec;
         return PHOS_OK;
     }

@@ -53,6 +53,30 @@ struct TableDev {
 
 constexpr uint32_t kMaxTable = 32768;  // three-level warp search limit
 
+// The protocol's response to one validation, applied by the validation
+// kernel's last CTA (no-sync sessions): kind 1 recopy (store victims with
+// flags[i] set become dirty[i] = 1), 2 CoW (a store victim with flags[i]
+// clear is a mis-speculation), 3 restore (a victim of any access with
+// flags[i] clear is one).  acc: u64[8] device words, [3] += violations,
+// [4] = first mis-speculated round (-1 = none), also published to the
+// mapped host word h_flag.  kind 0: no rule.
+struct ProtoRule {
+    const uint8_t *flags;
+    uint8_t *dirty;
+    uint64_t *acc;
+    int64_t *h_flag;
+    int64_t round;
+    uint32_t kind;
+};
+
+// phos_validate with an optional ProtoRule; *rule_fused = true when the
+// launched kernel applies it (otherwise the caller must).
+phos_status validate_impl(const phos_table_t *t, const uint8_t *d_perm, const uint64_t *d_trace,
+                          uint64_t n_rec, uint32_t access_bytes, uint32_t *d_bitmap,
+                          uint64_t *d_count, uint32_t *d_victim, uint32_t *d_victim_st,
+                          uint64_t *d_idx, uint64_t idx_cap, uint32_t *d_status,
+                          phos_stream_t stream, const ProtoRule *rule, bool *rule_fused);
+
 }  // namespace phos
 
 struct phos_table {

@@ -44,6 +44,7 @@ constexpr uint32_t kMaxStages = 8;
 constexpr uint64_t kRsvdMask = 0x3Full << 57;
 
 struct ValParams {
+    ProtoRule rule{};   // kind 0: none (see ProtoRule)
     TableDev tab;
     const uint8_t *perm;
     const uint64_t *trace;
@@ -514,12 +515,34 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     if (!*last) return;
     __threadfence();
     sum_cta_counts(p.cta_cnt, G, tid, red);
+    // the word after *last in dynamic shared memory (static shared memory
+    // would cut into the 227 KB dynamic opt-in)
+    volatile uint32_t *s_hit = last + 1;
+    const uint32_t rk = p.rule.kind;
+    if (rk) {
+        if (tid == 0) *s_hit = 0;
+        __syncthreads();
+    }
     for (uint32_t i = tid; i < nvw; i += blockDim.x) {
         const uint32_t v = __ldcg(p.vacc + i), vs = __ldcg(p.vacc + nvw + i);
         if (p.victim) p.victim[i] = v;
         if (p.victim_st) p.victim_st[i] = vs;
         p.vacc[i] = 0;
         p.vacc[nvw + i] = 0;
+        if (rk) {
+            // the protocol's response to this validation (see ProtoRule)
+            uint32_t m = rk == 3 ? v : vs;
+            while (m) {
+                const uint32_t b = i * 32 + (uint32_t)(__ffs(m) - 1);
+                m &= m - 1;
+                if (b >= n) break;
+                if (rk == 1) {
+                    if (p.rule.flags[b]) p.rule.dirty[b] = 1;
+                } else if (!p.rule.flags[b]) {
+                    *s_hit = 1;
+                }
+            }
+        }
     }
     __syncthreads();
     if (tid == 0) {
@@ -527,6 +550,15 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         p.count[1] = red[1];
         p.count[2] = red[2];
         *p.ticket = 0;
+        if (rk) {
+            uint64_t *acc = p.rule.acc;
+            acc[3] += red[0];
+            if (rk != 1 && *s_hit && (int64_t)acc[4] < 0) {
+                acc[4] = (uint64_t)p.rule.round;
+                *(volatile int64_t *)p.rule.h_flag = p.rule.round;
+                __threadfence_system();
+            }
+        }
     }
 }
 
@@ -656,12 +688,13 @@ extern "C" phos_status phos_validate_grid(uint32_t ctas) {
     return PHOS_OK;
 }
 
-extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
-                                     const uint64_t *d_trace, uint64_t n_rec,
-                                     uint32_t access_bytes, uint32_t *d_bitmap,
-                                     uint64_t *d_count, uint32_t *d_victim,
-                                     uint32_t *d_victim_st, uint64_t *d_idx, uint64_t idx_cap,
-                                     uint32_t *d_status, phos_stream_t stream) {
+phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
+                                const uint64_t *d_trace, uint64_t n_rec, uint32_t access_bytes,
+                                uint32_t *d_bitmap, uint64_t *d_count, uint32_t *d_victim,
+                                uint32_t *d_victim_st, uint64_t *d_idx, uint64_t idx_cap,
+                                uint32_t *d_status, phos_stream_t stream, const ProtoRule *rule,
+                                bool *rule_fused) {
+    if (rule_fused) *rule_fused = false;
     if (!t) return fail(PHOS_EINVAL, "validate: table is NULL");
     if (!d_count) return fail(PHOS_EINVAL, "validate: d_count is NULL");
     if (access_bytes == 0) return fail(PHOS_EINVAL, "validate: access_bytes is 0");
@@ -706,6 +739,10 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
     p.nvw = nvw;
     p.stages = 0;
     p.wpb = wpb;
+    if (rule && variant != 1 && n_rec) {
+        p.rule = *rule;
+        if (rule_fused) *rule_fused = true;
+    }
     static bool attr_done[4] = {false, false, false, false};
     auto attr = [&](const void *fn, int slot) -> phos_status {
         if (!attr_done[slot]) {
@@ -747,6 +784,16 @@ extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_per
         PHOS_CUDA(cudaGetLastError());
     }
     return PHOS_OK;
+}
+
+extern "C" phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
+                                     const uint64_t *d_trace, uint64_t n_rec,
+                                     uint32_t access_bytes, uint32_t *d_bitmap,
+                                     uint64_t *d_count, uint32_t *d_victim,
+                                     uint32_t *d_victim_st, uint64_t *d_idx, uint64_t idx_cap,
+                                     uint32_t *d_status, phos_stream_t stream) {
+    return validate_impl(t, d_perm, d_trace, n_rec, access_bytes, d_bitmap, d_count, d_victim,
+                         d_victim_st, d_idx, idx_cap, d_status, stream, nullptr, nullptr);
 }
 
 // ----------------------------------------------------------------------
