@@ -8,12 +8,11 @@
 // synchronisations that after_kernel performs anyway to read the victims.
 //
 // No-sync checkpoint sessions (PHOS_CKPT_NO_SYNC) take that round trip out:
-// after_kernel enqueues the validation, whose last CTA (or, after the
-// ring variant, a one-CTA rule kernel) applies the protocol's response on
-// the device (recopy: store victims
-// that were in flight or done become dirty; CoW: the first round with a
-// store victim neither done nor shadowed is recorded and published to a
-// mapped host word), and returns at once.  Every host decision of a round
+// after_kernel enqueues the validation, whose last CTA (or, after the ring
+// variant, a one-CTA rule kernel) applies the protocol's response on the
+// device (recopy: store victims that were in flight or done become dirty;
+// CoW: the first round with a store victim neither done nor shadowed is
+// recorded and published to a mapped host word), and returns at once.  Every host decision of a round
 // (copier pieces, CoW set, staging, dirty marks of speculated writes)
 // depends only on the speculation and on earlier host decisions, never on
 // a validation result, so the host can run ahead of the device; it learns
