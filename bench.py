@@ -485,7 +485,7 @@ def run_gpu(args, rank, world):
                 {"kernel": "k_validate_b, one launch per kernel trace (1.3M records)",
                  "bound": "hbm", "achieved": val_gbs, "peak": hbm, "unit": "GB/s",
                  "frac": val_gbs / hbm,
-                 "traffic": 10.487808e6 * (val_recs / len(dp.kernels)) / 1.3e6,
+                 "traffic": 10.488064e6 * (val_recs / len(dp.kernels)) / 1.3e6,
                  "accesses_per_s": val_recs / (val_ms * 1e-3), "avg_launch_us": val_launch_us,
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                  "traffic_source": "profiles/validate_b_one_trace_1p3M.md (ncu DRAM bytes of "
@@ -493,7 +493,7 @@ def run_gpu(args, rank, world):
                 {"kernel": "k_validate_b, one launch over 50 traces (65M records, union of "
                            "their speculated sets)",
                  "bound": "hbm", "achieved": cat_gbs, "peak": hbm, "unit": "GB/s",
-                 "frac": cat_gbs / hbm, "traffic": cat_n * 1.735669e9 / 208e6,
+                 "frac": cat_gbs / hbm, "traffic": cat_n * 1.736113e9 / 208e6,
                  "traffic_source": "profiles/validate_b_training_trace_208M.md (ncu DRAM bytes "
                                    "of 208M records), scaled by records",
                  "accesses_per_s": cat_n / (cat_ms * 1e-3), "launch_us": 1e3 * cat_ms},
