@@ -113,8 +113,10 @@ typedef struct phos_table phos_table_t;
 
 /* Copy n buffers (host array, sorted by base, disjoint, size > 0, inside
  * the 57-bit address space) into a device-resident table.  Synchronous.
- * EINVAL if the rules are broken; n may be 0 (every access then fails
- * validation as unmapped).  The table keeps a host copy for speculation. */
+ * At most 32,768 buffers (the validation kernels' three-level search).
+ * EINVAL if the rules are broken, checked on the host before any device
+ * work; n may be 0 (every access then fails validation as unmapped).  The
+ * table keeps a host copy for speculation. */
 phos_status phos_table_create(const phos_buf_t *bufs, uint32_t n, phos_table_t **out);
 phos_status phos_table_destroy(phos_table_t *t);
 uint32_t phos_table_size(const phos_table_t *t);

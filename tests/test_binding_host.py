@@ -42,3 +42,20 @@ def test_flattened_words_reproduce_oracle_rows():
               for k in kinds[off[l]:off[l + 1]]]
         assert np.array_equal(core.speculate(base, size, wa, wk),
                               core.speculate(base, size, args, kd))
+
+
+def test_table_rules_rejected_on_host():
+    """The table rules (sorted, disjoint, size > 0, 57-bit addresses, at most
+    32,768 buffers) are checked before any device work."""
+    import pytest
+    n = 100
+    base = (np.arange(n, dtype=np.uint64) * 4096 + np.uint64(1 << 40))
+    size = np.full(n, 256, np.uint64)
+    bad = [(base[::-1].copy(), size), (base, np.full(n, 8192, np.uint64)),
+           (base, np.zeros(n, np.uint64)), (base + np.uint64(1 << 57), size)]
+    big = (np.arange(32769, dtype=np.uint64) * 4096 + np.uint64(1 << 40))
+    bad.append((big, np.full(32769, 256, np.uint64)))
+    for b, sz in bad:
+        with pytest.raises(phos.PhosError) as e:
+            phos.Table(b, sz)
+        assert e.value.code == phos.PHOS_EINVAL

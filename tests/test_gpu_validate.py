@@ -76,6 +76,20 @@ def test_table_sizes_coalesced_runs(n, seed):
     check(t, base, lay.size, perm, rec, 4, idx_cap=300)
 
 
+def test_largest_table():
+    """The largest table the kernels take (32,768 buffers: three search
+    levels, the table in global memory), both validation variants (the
+    module's fixture)."""
+    rng, lay, base, t = layout_table(32768, 11, lo=256, hi=8192)
+    reads, writes = wl.pick_sets(rng, 32768, 1, 40)
+    perm = np.zeros(32768, np.uint8)
+    perm[reads] = phos.PERM_R
+    perm[writes] = phos.PERM_RW
+    rec, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, 20_003, stray_frac=0.02,
+                              stray_store_frac=0.3)
+    check(t, base, lay.size, perm, rec, 4, idx_cap=500)
+
+
 @pytest.mark.parametrize("w", [1, 2, 8, 16])
 def test_widths_and_straddles(w):
     rng, lay, base, t = layout_table(200, 20 + w, lo=256, hi=4096)
