@@ -665,7 +665,11 @@ def run_batched(args, rank, world):
             "speedup_vs_plain": plain_ms / plan_ms,
             "roofline": {"kernel": "k_plan (validation + D2D copies, one graph launch)",
                          "bound": "hbm", "achieved": alg / (plan_ms * 1e6), "peak": hbm,
-                         "unit": "GB/s", "frac": alg / (plan_ms * 1e6) / hbm, "traffic": None,
+                         "unit": "GB/s", "frac": alg / (plan_ms * 1e6) / hbm,
+                         "traffic": alg * 3.250291e9 / 3.300975e9,
+                         "traffic_source": "profiles/plan_batched_64img_4GB.md (ncu DRAM bytes "
+                                           "= 0.985 x algorithmic at one tenth of the size), "
+                                           "scaled to this launch",
                          "algorithmic_bytes": alg},
             "status": info["status"], "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
