@@ -9,7 +9,9 @@ Pins (tests/test_oracle_pins.py):
                small VA window, struct-chunk and one-past-end special cases
   validate   - brute force over a 64 KiB VA window x {load, store} x widths,
                generator ground-truth labels, closed-form special cases
-  digest     - closed form on hand-built words, permutation invariance
+  digest     - published SplitMix64 outputs on hand-built words (pins the
+               word-index term), zero padding of the tail
+  stray      - published SplitMix64 outputs
   mutator    - SplitMix64 reference outputs (published test vector)
 """
 import ctypes

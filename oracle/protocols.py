@@ -40,7 +40,9 @@ the CUDA control plane shares with this file):
     part of it; when the kernels run out first the copier drains the rest
   - restore: the protocol ends once every buffer is present; the remaining
     kernels then run normally
-Parity: pinned by the correctness theorems (image == memory at t1 for CoW,
+Parity: the copier's piece schedule is pinned by a piece log written out
+by hand (sizes that are not multiples of 256); the protocols are pinned by
+the correctness theorems (image == memory at t1 for CoW,
 at t2 for recopy; concurrent restore == stop-the-world restore + replay),
 by the worked scenarios of Figures 6, 7 and 9, and by closed-form special
 cases (zero staging budget, zero kernels, copier faster than the kernels).

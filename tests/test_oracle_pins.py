@@ -51,6 +51,47 @@ def test_digest_properties():
     assert core.digest(one) == core.mix64(5)
 
 
+def _published_sm0():
+    return [int(l, 16) for l in open(os.path.join(GOLD, "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+
+
+def test_digest_word_index_term_published():
+    """The word-index term j * GOLDEN of the digest, pinned by published
+    SplitMix64 outputs: mix64(x + GOLDEN) is the first output of a
+    generator in state x, so word j holding 0 contributes the (j)-th
+    output of the state-0 sequence, and a word holding GOLDEN at index 0
+    contributes the first output too.  A digest that used j (or no index)
+    in place of j * GOLDEN fails here."""
+    v = _published_sm0()
+    M = 2**64 - 1
+    G = 0x9E3779B97F4A7C15
+    w = lambda *xs: np.array(xs, np.uint64).view(np.uint8)
+    # mix64(0) = 0: a zero word at index 0 adds nothing
+    assert core.digest(w(0)) == 0
+    assert core.digest(w(G, 0)) == (2 * v[0]) & M
+    assert core.digest(w(G, 0, 0)) == (2 * v[0] + v[1]) & M
+    assert core.digest(w(0, 0, 0, 0)) == (v[0] + v[1] + v[2]) & M
+    # word j holding -j*GOLDEN + GOLDEN contributes the first output at every j
+    words = [((1 - j) * G) & M for j in range(5)]
+    assert core.digest(w(*words)) == (5 * v[0]) & M
+    # a 4-byte tail is zero-padded into the last word
+    assert core.digest(w(G, 0)[:12]) == (2 * v[0]) & M
+
+
+def test_stray_value_published():
+    """Stray store value (u32)sm(sm(seed ^ k) ^ r), pinned by published
+    outputs: with seed ^ k = 0 the inner value is the first state-0
+    output v0, so r = v0 gives sm(0) = v0 and r = v0 ^ GOLDEN gives
+    sm(GOLDEN) = v1 (low 32 bits of each)."""
+    v = _published_sm0()
+    G = 0x9E3779B97F4A7C15
+    assert core.stray_value(0, 0, v[0]) == v[0] & 0xFFFFFFFF == 0x7B1DCDAF
+    assert core.stray_value(0, 0, v[0] ^ G) == v[1] & 0xFFFFFFFF
+    assert core.stray_value(12345, 12345, v[0]) == v[0] & 0xFFFFFFFF   # only seed ^ k enters
+    assert core.stray_value(12345, 12344, v[0]) != v[0] & 0xFFFFFFFF
+
+
 def _owner_map(base, size, lo, hi):
     """owner[x - lo] = buffer index owning byte x, -1 in gaps."""
     own = np.full(hi - lo, -1, np.int64)

@@ -287,6 +287,54 @@ def test_restore_planted_mistake_is_caught(monkeypatch):
     assert not np.array_equal(got, ref)
 
 
+def _copier_log(sizes, chunk, quota, rounds, skip=lambda i: False, done=()):
+    cp = P.Copier(len(sizes), sizes, chunk)
+    for i in done:
+        cp.state[i] = P.DONE
+        cp.copied[i] = sizes[i]
+    for r in range(rounds):
+        cp.advance(quota, lambda i, off, ln: False, r, skip)
+    return [e[:4] for e in cp.log], cp.done()
+
+
+def test_copier_piece_schedule_by_hand():
+    """The copier's pieces written out by hand (Section 4.2 copy phase; the
+    4 MB chunking of Section 5, here 1 KiB): sizes that are not multiples
+    of 256, chunk 1024, quota 1536 per round.  Shows that a piece charges
+    align256(len) against the quota (300 -> 512, 904 -> 1024, 257 -> 512),
+    is cut at the quota left in the round (512-byte pieces), never crosses
+    into the next buffer (904 = the rest of buffer 1), and that the cursor
+    moves on to the next buffer within a round."""
+    log, done = _copier_log([300, 5000, 257], 1024, 1536, 4)
+    assert log == [
+        (0, 0, 0, 300), (0, 1, 0, 1024),
+        (1, 1, 1024, 1024), (1, 1, 2048, 512),
+        (2, 1, 2560, 1024), (2, 1, 3584, 512),
+        (3, 1, 4096, 904), (3, 2, 0, 257),
+    ]
+    assert done
+    # one round short: not done, buffer 2 untouched
+    log, done = _copier_log([300, 5000, 257], 1024, 1536, 3)
+    assert len(log) == 6 and not done
+
+
+def test_copier_cursor_skips_done_and_skipped_buffers():
+    """Buffers already done (a direct CoW copy, an on-demand restore) or
+    skipped (present) cost no quota: the cursor passes them in the same
+    round."""
+    log, done = _copier_log([300, 5000, 257], 1024, 1536, 1, skip=lambda i: i == 1)
+    assert log == [(0, 0, 0, 300), (0, 2, 0, 257)] and done
+    log, done = _copier_log([300, 5000, 257, 700], 1024, 1536, 1, done=(0, 2))
+    assert log == [(0, 1, 0, 1024), (0, 1, 1024, 512)] and not done
+    # an in-flight buffer finished elsewhere (on-demand restore of its
+    # remaining bytes) is not copied again
+    cp = P.Copier(2, [2048, 600], 1024)
+    cp.advance(1024, lambda i, off, ln: False, 0)
+    cp.copied[0], cp.state[0] = 2048, P.DONE
+    cp.advance(1024, lambda i, off, ln: False, 1)
+    assert [e[:4] for e in cp.log] == [(0, 0, 0, 1024), (1, 1, 0, 600)]
+
+
 def test_first_fit_allocator():
     a = P.FirstFit(1024)
     assert a.alloc(256) == 0 and a.alloc(512) == 256 and a.alloc(512) is None
