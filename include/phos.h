@@ -191,9 +191,14 @@ phos_status phos_validate(const phos_table_t *t, const uint8_t *d_perm,
  * every GPU which loads the library holds until the process exits.
  * Limits: tables of at most 16384 buffers (larger ones get PHOS_EINVAL and
  * a message; use phos_validate for them) and at most 256 CTAs per launch
- * (the call never launches more).  The first call on a device looks the array up on
- * that device (it makes the device current for the lookup and restores
- * the previous one); make that first call before any stream capture.
+ * (the call never launches more).  The process-wide settings of
+ * phos_validate_config and phos_validate_grid do not apply here: this call
+ * always runs the batched-leader kernel on min(SMs, 256) CTAs (same
+ * results, possibly different timing).  The table's device must be the
+ * calling thread's current device (else PHOS_EINVAL, nothing launched):
+ * the call never switches devices.  The first call on a device looks up
+ * the array's address there; make that first call before any stream
+ * capture.
  * Every call clears the parts of the array it uses, then launches; all
  * calls share the one array, so calls that overlap on the GPU (concurrent
  * streams, or several host threads) race and must be ordered by the

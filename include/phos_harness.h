@@ -78,6 +78,17 @@ phos_status phos_harness_drive_ckpt(phos_ckpt_t *c, const phos_table_t *t, uint6
  * used to give live memory and arenas a reproducible initial content. */
 phos_status phos_harness_fill(uint64_t ptr, uint64_t len, uint64_t key, phos_stream_t stream);
 
+/* Test hooks on a table handle.
+ * phos_harness_table_rebind records `device` as the device the table
+ * belongs to (the previous value in *old_device, nullable); nothing is
+ * moved, so the table is only usable again once the true device is
+ * recorded back.  It lets a one-GPU test reach the device-mismatch
+ * rejection of calls that must not switch devices.
+ * phos_harness_table_scratch reports the bytes of the table's growable
+ * validation scratch (0 until a call has needed it). */
+phos_status phos_harness_table_rebind(phos_table_t *t, int device, int *old_device);
+phos_status phos_harness_table_scratch(const phos_table_t *t, uint64_t *val_bytes);
+
 #ifdef __cplusplus
 }
 #endif

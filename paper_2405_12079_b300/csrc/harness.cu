@@ -291,3 +291,19 @@ extern "C" phos_status phos_harness_drive_ckpt(phos_ckpt_t *c, const phos_table_
     if (kernels_run) *kernels_run = k;
     return r;
 }
+
+// Test hooks on a table handle (see phos_harness.h).
+extern "C" phos_status phos_harness_table_rebind(phos_table_t *t, int device, int *old_device) {
+    if (!t) return fail(PHOS_EINVAL, "harness_table_rebind: table is NULL");
+    if (old_device) *old_device = t->device;
+    t->device = device;
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_harness_table_scratch(const phos_table_t *t, uint64_t *val_bytes) {
+    if (!t || !val_bytes) return fail(PHOS_EINVAL, "harness_table_scratch: NULL argument");
+    phos_table *T = const_cast<phos_table *>(t);
+    std::lock_guard<std::mutex> g(T->mu);
+    *val_bytes = T->val_scratch.bytes;
+    return PHOS_OK;
+}

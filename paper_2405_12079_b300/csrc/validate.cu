@@ -832,18 +832,14 @@ __global__ void k_noalloc_clear(uint8_t *scratch, uint32_t nvw) {
     for (uint32_t i = threadIdx.x; i < 2 * nvw; i += blockDim.x) vacc[i] = 0;
 }
 
-// Device address of the array on the table's device, looked up once per
-// device with that device current.
+// Device address of the array on `device`, which the caller has checked is
+// the current device; looked up once per device.
 static phos_status noalloc_scratch(int device, void **out) {
     if (device < 0 || device >= 64) return fail(PHOS_EINVAL, "validate_noalloc: device %d", device);
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     if (!g_noalloc_ptr[device]) {
-        int cur = -1;
-        PHOS_CUDA(cudaGetDevice(&cur));
-        if (cur != device) PHOS_CUDA(cudaSetDevice(device));
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (cur != device) cudaSetDevice(cur);
         if (e != cudaSuccess) return cuda_fail(e, "validate_noalloc: cudaGetSymbolAddress");
         g_noalloc_ptr[device] = p;
     }
@@ -874,6 +870,15 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
                     "validate_noalloc: table of %u buffers exceeds the fixed scratch limit of %u "
                     "buffers; use phos_validate",
                     t->n, kNoallocMaxBuffers);
+    // The kernels launch on the calling thread's current device, so that
+    // must be the device the table (and the array's address) belongs to.
+    int cur = -1;
+    PHOS_CUDA(cudaGetDevice(&cur));
+    if (cur != t->device)
+        return fail(PHOS_EINVAL,
+                    "validate_noalloc: the table belongs to device %d but device %d is current; "
+                    "make device %d current before the call",
+                    t->device, cur, t->device);
     void *scr = nullptr;
     phos_status r = noalloc_scratch(t->device, &scr);
     if (r) return r;

@@ -60,6 +60,8 @@ _SIGS = {
     "phos_harness_mutate": (_i32, [_vp, _u64, _u64, _vp, _u32, _vp, _u32, _vp, _u32, _vp]),
     "phos_harness_drive_ckpt": (_i32, [_vp, _vp, _u64, _u64, _vp, _u32, _vp, _P(_u32)]),
     "phos_harness_fill": (_i32, [_u64, _u64, _u64, _vp]),
+    "phos_harness_table_rebind": (_i32, [_vp, _i32, _P(_i32)]),
+    "phos_harness_table_scratch": (_i32, [_vp, _P(_u64)]),
     "phos_plan_create": (_i32, [_vp, _u32, _P(_vp)]),
     "phos_plan_launch": (_i32, [_vp, _vp]),
     "phos_plan_set_tile": (_i32, [_vp, _u64]),
@@ -374,6 +376,21 @@ def harness_drive_ckpt(ckpt, table, seed, quota, kernels, stream=None):
 
 def harness_fill(ptr, length, key, stream=None):
     return check(lib().phos_harness_fill(ptr, length, key & (2**64 - 1), stream), "harness_fill")
+
+
+def harness_table_rebind(table, device):
+    """Test hook: record ``device`` as the table's device; returns the old one."""
+    old = _i32()
+    check(lib().phos_harness_table_rebind(table.handle, device, _c.byref(old)),
+          "harness_table_rebind")
+    return int(old.value)
+
+
+def harness_table_scratch(table):
+    """Bytes of the table's growable validation scratch."""
+    b = _u64()
+    check(lib().phos_harness_table_scratch(table.handle, _c.byref(b)), "harness_table_scratch")
+    return int(b.value)
 
 
 def _stats_dict(st):
