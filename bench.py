@@ -75,12 +75,77 @@ def oracle_sample(scale, n_kernels=200, seed=None):
     return moved, recs, dt
 
 
-def cpu_baseline(scale=0.04):
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or "unknown"
+
+
+def cpu_loops(moved_per_step, recs_per_step, copy_sample=2 << 30):
+    """The oracle's two hot loops on the host: validation (linear scan) of
+    one full-size 1.3M-record training trace over the 1,000-buffer table,
+    and a host memcpy of copy_sample bytes; each single-threaded and on
+    every host thread (oracle_omp.c).  The step's time on the CPU is
+    extrapolated from these rates: recs_per_step / validation rate +
+    moved_per_step / copy rate."""
+    from oracle import core
+    from paper_2405_12079_b300 import workloads as wl
+    cfg = wl.training(scale=1.0, n_kernels=1)
+    rng, lay = cfg["rng"], cfg["layout"]
+    va0 = 0x7F00_0000_0000
+    reads, writes = wl.pick_sets(rng, lay.n)
+    perm = np.zeros(lay.n, np.uint8)
+    perm[reads] = 1
+    perm[writes] = 3
+    tr, _, _ = wl.trace_runs(rng, lay, va0, reads, writes, 1_300_000, 0.001, 0.0)
+    base = lay.base(va0)
+    src = np.empty(copy_sample, np.uint8)
+    src[::4096] = 1                                  # touch every page
+    dst = np.empty_like(src)
+    dst[::4096] = 0
+    out = {}
+    t = time.perf_counter()
+    core.validate(base, lay.size, perm, tr, 4)
+    v1 = len(tr) / (time.perf_counter() - t)
+    t = time.perf_counter()
+    np.copyto(dst, src)
+    c1 = copy_sample / (time.perf_counter() - t)
+    t = time.perf_counter()
+    core.validate_omp(base, lay.size, perm, tr, 4)
+    vn = len(tr) / (time.perf_counter() - t)
+    core.memcpy_omp(dst, src)                        # first touch of the threads' pages
+    t = time.perf_counter()
+    core.memcpy_omp(dst, src)
+    cn = copy_sample / (time.perf_counter() - t)
+    for key, v, c, th in (("single_thread", v1, c1, 1), ("all_cores", vn, cn, core.omp_threads())):
+        step_s = recs_per_step / v + moved_per_step / c
+        out[key] = {"value": moved_per_step / step_s / 1e9, "unit": "GB/s", "cores": th,
+                    "validated_accesses_per_s": v, "memcpy_GBs": c / 1e9,
+                    "step_s_extrapolated": step_s}
+    out["sample"] = ("validation of one 1.3M-record training trace over the 1,000-buffer table "
+                     "(linear scan) and a %.1f GB host memcpy, each timed single-threaded and "
+                     "on every host thread; the step (%d records validated, %.1f GB moved) is "
+                     "extrapolated from those rates" % (copy_sample / 1e9, recs_per_step,
+                                                       moved_per_step / 1e9))
+    return out
+
+
+def cpu_baseline(scale=0.04, moved_per_step=None, recs_per_step=None):
     moved, recs, dt = oracle_sample(scale)
-    return {"value": moved / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+    line = {"value": moved / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(), "host_threads": os.cpu_count(),
             "sample": "oracle CoW + recopy checkpoint of the same workload scaled to %.1f%% "
-                      "(%.0f MB image, %d records validated), single thread, %.1f s"
+                      "(%.0f MB image, %d records validated), single thread, %.1f s; the "
+                      "full-size figure is extrapolated as this rate"
                       % (100 * scale, 40e3 * scale, recs, dt)}
+    if moved_per_step:
+        line["loops"] = cpu_loops(moved_per_step, recs_per_step)
+    return line
 
 
 def run_reference(args, rank, world):
@@ -448,7 +513,8 @@ def run_gpu(args, rank, world):
     d2h_step = int((d2h_bytes + direct_bytes) / args.steps)
 
     if rank == 0:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(moved_per_step=tot_moved / args.steps / world,
+                           recs_per_step=tot_recs / args.steps / world)
         legs = ("DMA engines (cudaMemcpyAsync) for pieces >= 1 MiB, k_copy_main for smaller "
                 "ones" if args.host_copy == "dma" else "k_copy_main (SM-issued stores)")
         roof = {"kernel": "host legs of the background copier and recopy, device -> pinned "

@@ -32,9 +32,66 @@ u8p = ctypes.POINTER(ctypes.c_uint8)
 def build(force=False):
     """Compile phos_oracle.c with gcc into oracle/liboracle.so."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O1", "-std=c99", "-Wall", "-shared", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-shared", "-fPIC",
                                "-o", _LIB, _SRC])
     return _LIB
+
+
+_OMP_SRC = os.path.join(_HERE, "oracle_omp.c")
+_OMP_LIB = os.path.join(_HERE, "liboracle_omp.so")
+_omp = None
+
+
+def build_omp(force=False):
+    """Compile the all-core timing driver (oracle_omp.c + phos_oracle.c,
+    OpenMP) into oracle/liboracle_omp.so; used only to time the baseline."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_OMP_SRC))
+    if force or not os.path.exists(_OMP_LIB) or os.path.getmtime(_OMP_LIB) < newest:
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-Wall", "-fopenmp", "-shared",
+                               "-fPIC", "-o", _OMP_LIB, _OMP_SRC, _SRC])
+    return _OMP_LIB
+
+
+def omp_lib():
+    global _omp
+    if _omp is None:
+        build_omp()
+        L = ctypes.CDLL(_OMP_LIB)
+        L.orc_threads.restype = ctypes.c_int
+        L.orc_validate_omp.restype = ctypes.c_int
+        L.orc_validate_omp.argtypes = [u64p, u64p, u8p, ctypes.c_uint32, u64p, ctypes.c_uint64,
+                                       ctypes.c_uint32, u32p, u64p, u32p, u32p]
+        L.orc_memcpy_omp.restype = None
+        L.orc_memcpy_omp.argtypes = [u8p, u8p, ctypes.c_uint64]
+        _omp = L
+    return _omp
+
+
+def omp_threads():
+    return int(omp_lib().orc_threads())
+
+
+def validate_omp(base, size, perm, trace, w):
+    """orc_validate run on every host thread over word-aligned ranges of the
+    trace (timing only; results equal validate's, without the index list)."""
+    base, size = _u64(base), _u64(size)
+    perm = np.ascontiguousarray(perm, np.uint8)
+    trace = _u64(trace)
+    n, N = len(base), len(trace)
+    bitmap = np.zeros(max((N + 31) // 32, 1), np.uint32)
+    count = np.zeros(3, np.uint64)
+    victim = np.zeros(max((n + 31) // 32, 1), np.uint32)
+    victim_st = np.zeros(max((n + 31) // 32, 1), np.uint32)
+    omp_lib().orc_validate_omp(_p(base, u64p), _p(size, u64p), _p(perm, u8p), n,
+                               _p(trace, u64p), N, w, _p(bitmap, u32p), _p(count, u64p),
+                               _p(victim, u32p), _p(victim_st, u32p))
+    nv = (n + 31) // 32
+    return bitmap[:(N + 31) // 32], count, victim[:nv], victim_st[:nv]
+
+
+def memcpy_omp(dst, src):
+    assert dst.dtype == np.uint8 and src.dtype == np.uint8 and dst.size == src.size
+    omp_lib().orc_memcpy_omp(_p(dst, u8p), _p(src, u8p), src.size)
 
 
 def lib():
@@ -65,6 +122,12 @@ def lib():
         L.orc_mutator_seed.argtypes = [ctypes.c_uint64, ctypes.c_uint64, u64p, ctypes.c_uint32]
         L.orc_mutator_fill.restype = None
         L.orc_mutator_fill.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]
+        L.orc_digest_at.restype = ctypes.c_uint64
+        L.orc_digest_at.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_words.restype = None
+        L.orc_words.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+        L.orc_mutator_key.restype = ctypes.c_uint64
+        L.orc_mutator_key.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
         L.orc_stray_value.restype = ctypes.c_uint32
         L.orc_stray_value.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
         _lib = L
@@ -155,6 +218,19 @@ def digest(buf):
     return int(lib().orc_digest(_p(b, u8p), b.size))
 
 
+def digest_at(buf, j0):
+    """Partial digest of a piece starting at word j0 of its buffer."""
+    b = np.ascontiguousarray(buf, np.uint8)
+    return int(lib().orc_digest_at(_p(b, u8p), b.size, j0 & 0xFFFFFFFFFFFFFFFF))
+
+
+def words(length, key, byte_off=0):
+    """Bytes [byte_off, byte_off + length) of the word stream sm(key ^ j)."""
+    out = np.empty(int(length), np.uint8)
+    lib().orc_words(_p(out, u8p), out.size, key & 0xFFFFFFFFFFFFFFFF, int(byte_off))
+    return out
+
+
 def mutator_seed(seed, k, read_digests):
     d = _u64(read_digests) if len(read_digests) else np.zeros(1, np.uint64)
     return int(lib().orc_mutator_seed(seed, k, _p(d, u64p), len(read_digests)))
@@ -164,6 +240,11 @@ def mutator_fill(view, s_k, w):
     """Fill a writable uint8 numpy view in place (harness mutator)."""
     assert view.flags["C_CONTIGUOUS"] and view.dtype == np.uint8
     lib().orc_mutator_fill(_p(view, u8p), view.size, s_k, w)
+
+
+def mutator_key(s_k, w):
+    """Key of the word stream the mutator writes into buffer w."""
+    return int(lib().orc_mutator_key(s_k & 0xFFFFFFFFFFFFFFFF, int(w)))
 
 
 def stray_value(seed, k, r):

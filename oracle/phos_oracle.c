@@ -17,7 +17,7 @@
  *   - trace record: bit 63 = store, bits 57..62 reserved (must be 0),
  *     bits 0..56 = address; every access is w bytes wide   (Section 4.1)
  *
- * Build: gcc -O1 -shared -fPIC -o liboracle.so phos_oracle.c
+ * Build: gcc -O2 -shared -fPIC -o liboracle.so phos_oracle.c
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -176,6 +176,38 @@ uint64_t orc_digest(const uint8_t *p, uint64_t len) {
     return acc;
 }
 
+/* The digest's partial sum over a piece of a buffer whose first byte is
+ * the first byte of the buffer's word j0 (so a buffer's digest is the
+ * mod-2^64 sum of its pieces' partial sums when every piece but the last
+ * is a whole number of words). */
+uint64_t orc_digest_at(const uint8_t *p, uint64_t len, uint64_t j0) {
+    uint64_t acc = 0;
+    for (uint64_t j = 0; 8 * j < len; j++) {
+        uint64_t wv = 0;
+        for (uint64_t t = 0; t < 8 && 8 * j + t < len; t++)
+            wv |= (uint64_t)p[8 * j + t] << (8 * t);
+        acc += orc_mix64(wv + (j0 + j) * ORC_GOLDEN);
+    }
+    return acc;
+}
+
+/* ---------------------------------------------------------------------
+ * Word stream of the harness fill (not in the paper): the byte stream
+ * whose 8-byte little-endian word j is sm(key ^ j).  orc_words writes its
+ * bytes [byte_off, byte_off + len) to out.  The mutator's fill of buffer
+ * w is this stream with key = sm(s_k ^ sm(w)) from byte 0; the initial
+ * fill of a memory arena is this stream with the arena's key.
+ * ------------------------------------------------------------------- */
+void orc_words(uint8_t *out, uint64_t len, uint64_t key, uint64_t byte_off) {
+    uint64_t q = 0;
+    while (q < len) {
+        uint64_t b = byte_off + q;
+        uint64_t v = orc_sm(key ^ (b >> 3));
+        for (uint64_t t = b & 7; t < 8 && q < len; t++, q++)
+            out[q] = (uint8_t)(v >> (8 * t));
+    }
+}
+
 /* ---------------------------------------------------------------------
  * Mutator kernel k (harness standing in for an application kernel).
  *   s_k  = sm(seed ^ sm(k)); then s_k = sm(s_k ^ D(r)) for each read buffer
@@ -190,8 +222,10 @@ uint64_t orc_mutator_seed(uint64_t seed, uint64_t k, const uint64_t *rdig, uint3
     return s;
 }
 
+uint64_t orc_mutator_key(uint64_t s_k, uint32_t w) { return orc_sm(s_k ^ orc_sm((uint64_t)w)); }
+
 void orc_mutator_fill(uint8_t *p, uint64_t len, uint64_t s_k, uint32_t w) {
-    uint64_t key = orc_sm(s_k ^ orc_sm((uint64_t)w));
+    uint64_t key = orc_mutator_key(s_k, w);
     for (uint64_t j = 0; 8 * j < len; j++) {
         uint64_t v = orc_sm(key ^ j);
         for (uint64_t t = 0; t < 8 && 8 * j + t < len; t++)

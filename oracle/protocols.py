@@ -84,12 +84,22 @@ class Process:
     def speculate(self, kern):
         return core.speculate(self.base, self.size, kern.args, kern.kinds)
 
+    def new_bytes(self, n):
+        """A zeroed byte array for an image or a staging area."""
+        return np.zeros(int(n), np.uint8)
+
+    def read_digests(self, reads):
+        return [core.digest(self.buf(r)) for r in reads]
+
+    def fill(self, w, s_k):
+        core.mutator_fill(self.buf(w), s_k, int(w))
+
     def run_kernel(self, k, kern):
         """Harness mutator: read digests, fill written buffers, strays."""
-        digs = [core.digest(self.buf(r)) for r in kern.reads]
+        digs = self.read_digests(kern.reads)
         s = core.mutator_seed(self.seed, k, digs)
         for w in kern.writes:
-            core.mutator_fill(self.buf(w), s, int(w))
+            self.fill(w, s)
         for r, a in kern.strays:
             v = core.stray_value(self.seed, k, int(r))
             o = int(a) - self.va0
@@ -106,7 +116,7 @@ def victims_of(res, n):
 
 
 def stw_checkpoint(proc):
-    img = np.zeros(proc.image_bytes, np.uint8)
+    img = proc.new_bytes(proc.image_bytes)
     for i in range(proc.n):
         s, io = int(proc.size[i]), int(proc.img_off[i])
         img[io:io + s] = proc.buf(i)
@@ -193,8 +203,8 @@ class Result:
 def cow_checkpoint(proc, kernels, staging_bytes, chunk, quota):
     """Section 4.2 soft copy-on-write checkpoint taken at t1 = now."""
     n = proc.n
-    image = np.zeros(proc.image_bytes, np.uint8)
-    staging = np.zeros(max(int(staging_bytes), 1), np.uint8)
+    image = proc.new_bytes(proc.image_bytes)
+    staging = proc.new_bytes(max(int(staging_bytes), 1))
     alloc = FirstFit(staging_bytes)
     shadow = [None] * n
     cp = Copier(n, proc.size, chunk)
@@ -267,7 +277,7 @@ def victims_of_store(proc, perm, kern, res):
 def recopy_checkpoint(proc, kernels, chunk, quota):
     """Section 4.3 soft recopy checkpoint started at t1 = now, ending at t2."""
     n = proc.n
-    image = np.zeros(proc.image_bytes, np.uint8)
+    image = proc.new_bytes(proc.image_bytes)
     cp = Copier(n, proc.size, chunk)
     dirty = set()
     stats = dict(copier_bytes=0, recopy_bytes=0)
@@ -320,7 +330,7 @@ def iterative_recopy(proc, kernels, chunk, quota, max_passes, stop_bytes):
     stop-the-world.  The pass starts in the round whose copier move
     finished the previous pass, before that round's kernel."""
     n = proc.n
-    image = np.zeros(proc.image_bytes, np.uint8)
+    image = proc.new_bytes(proc.image_bytes)
     cp = Copier(n, proc.size, chunk)
     dirty = set()
     passes = []                           # (round, buffers, bytes) of each extra pass
