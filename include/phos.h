@@ -215,6 +215,15 @@ phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_t *d_perm,
  * one of 32 words, the warp checks all 32 words against them).  Results
  * are identical; only speed differs. */
 phos_status phos_validate_config(uint32_t variant);
+/* Bound on the waits of the bulk-copy ring variant (variant 1) for a staged
+ * trace tile: the number of mbarrier probes before the wait gives up
+ * (default 2^24, far beyond any copy's latency).  A wait that gives up makes
+ * the CTA stop validating, wait (with the default bound) for its copies
+ * still in flight, and set PHOS_ETIMEDOUT in d_status; the outputs of that
+ * launch are then undefined and the device stays usable.  0 makes every
+ * such wait give up at once: a deterministic test of that path.
+ * Process-wide. */
+phos_status phos_validate_wait_limit(uint32_t probes);
 /* Grid of phos_validate: 0 (default) = one CTA per SM, else that many CTAs
  * (at most 4096; each CTA stages the table once).  Process-wide. */
 phos_status phos_validate_grid(uint32_t ctas);
@@ -367,7 +376,8 @@ typedef struct {
 } phos_request_t;
 
 typedef struct {
-    uint32_t state;               /* 0 queued, 1 admitted, 2 done, 3 failed  */
+    uint32_t state;               /* 0 queued, 1 admitted, 2 done, 3 failed,
+                                     4 cancelled                             */
     phos_status status;
     uint64_t bytes;               /* image bytes moved                       */
     uint64_t t_submit_ns;         /* CLOCK_MONOTONIC                         */
@@ -381,6 +391,16 @@ phos_status phos_server_start(const phos_server_desc_t *d, phos_server_t **out);
 phos_status phos_server_submit(phos_server_t *s, const phos_request_t *r, uint64_t *ticket);
 /* Non-blocking. */
 phos_status phos_server_poll(phos_server_t *s, uint64_t ticket, phos_result_t *out);
+/* Cancel a request (one of the failures a serving loop must survive; the
+ * other requests are not affected).  Queued: it leaves the queue at once
+ * (state 4).  Admitted: no further piece of it is issued; it ends (state 4)
+ * once its pieces already on the GPU have landed, and a checkpoint's
+ * staging is then released.  A request whose last piece was already issued
+ * completes normally (state 2), as does a finished one.  A cancelled
+ * checkpoint leaves its host image partly written, a cancelled restore its
+ * live buffers partly restored.  Non-blocking, thread-safe; EINVAL for an
+ * unknown ticket. */
+phos_status phos_server_cancel(phos_server_t *s, uint64_t ticket);
 /* Wait until nothing is queued or in flight (ETIMEDOUT after timeout_ms). */
 phos_status phos_server_drain(phos_server_t *s, uint32_t timeout_ms);
 /* Finish what was submitted, then stop the scheduler and free its streams. */
@@ -409,6 +429,7 @@ typedef struct {
                                      issue was held back for an application
                                      transfer                                */
     uint64_t batches;             /* C/R host-leg batches issued             */
+    uint64_t cancelled;           /* requests ended by phos_server_cancel    */
 } phos_server_stats_t;
 phos_status phos_server_stats(phos_server_t *s, phos_server_stats_t *out);
 

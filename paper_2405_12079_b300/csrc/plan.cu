@@ -137,24 +137,9 @@ __global__ void __launch_bounds__(kPlanThreads, 1) k_plan(const PlanDev P) {
             const uint64_t r0 = lb * kBatch;
             const uint64_t nb = min((uint64_t)kBatch, it.n_rec - r0);
             const uint64_t *recs = it.trace + r0;
-            {
-                Lead ld;
-                ld.b = 0;
-                ld.l = 0;
-                ld.i = -1;
-                ld.pm = 0;
-                if (lane * 32 < nb) {
-                    const uint64_t x = recs[lane * 32] & PHOS_REC_ADDR_MASK;
-                    const int i = L.lane_search(x);
-                    if (i >= 0) {
-                        ld.b = L.base[i];
-                        ld.l = L.lim[i];
-                        ld.i = i;
-                        ld.pm = L.perm[i];
-                    }
-                }
-                mine[lane] = ld;
-            }
+            mine[lane] = make_lead(
+                L, lane * 32 < nb ? L.lane_search(recs[lane * 32] & PHOS_REC_ADDR_MASK) : -1,
+                true);
             __syncwarp();
             uint32_t *bm = it.bitmap + (r0 >> 5);
             if (nb == kBatch)

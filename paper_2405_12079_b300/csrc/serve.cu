@@ -58,12 +58,15 @@ struct Req {
     uint64_t buf_off = 0;
     bool snap_done = false;
     cudaEvent_t snap_ev = nullptr;
+    bool cancel = false;           // phos_server_cancel on an admitted request
+    uint32_t inflight = 0;         // issued batches holding its pieces, not retired
 };
 
 // One batch issued on a host-leg stream.
 struct Issue {
     cudaEvent_t ev;
     std::vector<uint64_t> finishing;  // tickets whose last piece is in this batch
+    std::vector<uint64_t> members;    // tickets with pieces in this batch
 };
 
 // An application transfer the scheduler yields to.
@@ -205,7 +208,7 @@ struct phos_server {
         std::vector<Req *> cand;
         for (uint64_t tk : active) {
             Req &q = reqs[tk];
-            if (q.res.state != 1 || q.res.status) continue;
+            if (q.res.state != 1 || q.res.status || q.cancel) continue;
             if (d2h && q.r.kind == PHOS_REQ_CHECKPOINT && q.issued < q.img_bytes) {
                 if (!q.snap_done) {
                     if (cudaEventQuery(q.snap_ev) != cudaSuccess) continue;
@@ -261,6 +264,8 @@ struct phos_server {
         for (size_t c = 0; c < cand.size(); ++c) {
             if (lists[c].empty()) continue;
             Req &q = *cand[c];
+            is.members.push_back(q.ticket);
+            ++q.inflight;
             const phos_table *t = q.r.table;
             std::vector<phos_copy_t> kern;
             // Runs of pieces that are contiguous on both sides (adjacent
@@ -330,6 +335,7 @@ struct phos_server {
         while (!inf.empty() && cudaEventQuery(inf.front().ev) == cudaSuccess) {
             Issue &is = inf.front();
             const uint64_t t = now_ns();
+            for (uint64_t tk : is.members) --reqs[tk].inflight;
             for (uint64_t tk : is.finishing) {
                 Req &q = reqs[tk];
                 q.res.state = q.res.status ? 3 : 2;
@@ -346,6 +352,28 @@ struct phos_server {
         }
     }
 
+    // Admitted requests cancelled before their last piece was issued end
+    // once none of their pieces is in flight (and a checkpoint's snapshot
+    // has landed, so its staging can be reused).
+    void retire_cancelled() {
+        for (size_t k = 0; k < active.size();) {
+            Req &q = reqs[active[k]];
+            if (q.cancel && q.res.state == 1 && q.issued < q.img_bytes && q.inflight == 0 &&
+                (!q.snap_ev || cudaEventQuery(q.snap_ev) == cudaSuccess)) {
+                q.res.state = 4;
+                q.res.t_done_ns = now_ns();
+                if (q.r.kind == PHOS_REQ_CHECKPOINT && q.img_bytes)
+                    stg_release(q.stg_off, align_up(q.img_bytes, 256));
+                if (q.snap_ev) ev_pool.push_back(q.snap_ev);
+                q.snap_ev = nullptr;
+                ++st.cancelled;
+                active.erase(active.begin() + k);
+            } else {
+                ++k;
+            }
+        }
+    }
+
     void loop() {
         cudaSetDevice(device);
         std::unique_lock<std::mutex> lk(mu);
@@ -353,6 +381,7 @@ struct phos_server {
             retire(inflight_d2h);
             retire(inflight_h2d);
             retire_app();
+            retire_cancelled();
             admit();
             issue(true);
             issue(false);
@@ -438,6 +467,25 @@ extern "C" phos_status phos_server_submit(phos_server_t *S, const phos_request_t
     S->reqs[q.ticket] = q;
     S->queue.push_back(q.ticket);
     *ticket = q.ticket;
+    S->cv.notify_one();
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_server_cancel(phos_server_t *S, uint64_t ticket) {
+    if (!S) return fail(PHOS_EINVAL, "server_cancel: NULL server");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(PHOS_EINVAL, "server_cancel: unknown ticket");
+    Req &q = it->second;
+    if (q.res.state == 0) {
+        auto qi = std::find(S->queue.begin(), S->queue.end(), ticket);
+        if (qi != S->queue.end()) S->queue.erase(qi);
+        q.res.state = 4;
+        q.res.t_done_ns = now_ns();
+        ++S->st.cancelled;
+    } else if (q.res.state == 1) {
+        q.cancel = true;
+    }
     S->cv.notify_one();
     return PHOS_OK;
 }

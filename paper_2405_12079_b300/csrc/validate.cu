@@ -42,6 +42,7 @@ constexpr uint32_t kTileBytes = kTileRec * 8;
 constexpr uint32_t kValThreads = 1024;
 constexpr uint32_t kMaxStages = 8;
 constexpr uint64_t kRsvdMask = 0x3Full << 57;
+constexpr uint32_t kWaitLimit = 1u << 24;   // probes before a tile wait gives up
 
 struct ValParams {
     ProtoRule rule{};   // kind 0: none (see ProtoRule)
@@ -63,6 +64,7 @@ struct ValParams {
     uint32_t nvw;
     uint32_t stages;
     uint32_t wpb;       // batched variant: bitmap words per warp batch
+    uint32_t wait_limit;  // ring variant: probes of a staged tile's mbarrier
 };
 
 // Classify the 32 records of one bitmap word (one per lane) and write the
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
     uint32_t s = 0, par = 0;
     uint64_t r0 = t0 * kTileRec;
     for (uint32_t j = 0; j < ntl; ++j) {
-        if (!mbar_wait_bounded(&mbar[s], par)) {
+        if (!mbar_wait_bounded(&mbar[s], par, p.wait_limit)) {
             if (lane == 0) atomicOr(flag, 1u);
             break;
         }
@@ -415,23 +417,8 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
             const uint64_t nt = bt + nwarps;
             const bool more = nt < b1 && nt < nfull;
             Lead *ldp = mine + 32 * sel;
-            {
-                Lead ld;
-                ld.b = 0;
-                ld.l = 0;
-                ld.i = -1;
-                ld.pm = 0;
-                if (lane < W) {
-                    const int i = L.lane_search(xl & PHOS_REC_ADDR_MASK);
-                    if (i >= 0) {
-                        ld.b = L.base[i];
-                        ld.l = L.limit(i, kSmemTable);
-                        ld.i = i;
-                        ld.pm = L.perm[i];
-                    }
-                }
-                ldp[lane] = ld;
-            }
+            ldp[lane] = make_lead(L, lane < W ? L.lane_search(xl & PHOS_REC_ADDR_MASK) : -1,
+                                  kSmemTable);
             const uint64_t *rn = p.trace + (more ? nt : bt) * brec;
             xl = (more && lane < W) ? rn[lane * 32] : 0ull;
             // the next batch into L2 while this one is worked on (one batch
@@ -466,24 +453,10 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         const uint64_t nb = min(brec, p.n_rec - r0);
         const uint64_t *recs = p.trace + r0;
         // leaders: lane j searches the first record of word j
-        {
-            Lead ld;
-            ld.b = 0;
-            ld.l = 0;
-            ld.i = -1;
-            ld.pm = 0;
-            if (lane < W && lane * 32 < nb) {
-                const uint64_t x = recs[lane * 32] & PHOS_REC_ADDR_MASK;
-                const int i = L.lane_search(x);
-                if (i >= 0) {
-                    ld.b = L.base[i];
-                    ld.l = L.limit(i, kSmemTable);
-                    ld.i = i;
-                    ld.pm = L.perm[i];
-                }
-            }
-            mine[lane] = ld;
-        }
+        mine[lane] = make_lead(
+            L, (lane < W && lane * 32 < nb) ? L.lane_search(recs[lane * 32] & PHOS_REC_ADDR_MASK)
+                                            : -1,
+            kSmemTable);
         __syncwarp();
         uint32_t *bm = p.bitmap + (r0 >> 5);
         if (nb == brec)
@@ -650,6 +623,7 @@ static size_t plan_batched(uint32_t n, int device, bool *smem_table) {
 }
 
 static uint32_t g_val_variant = 0;  // 0 auto, 1 TMA ring, 2 batched leaders
+static uint32_t g_val_wait_limit = kWaitLimit;
 static uint32_t g_val_ctas = 0;     // 0 auto (one per SM), else the grid size
 
 // Words per warp batch: 32 (most amortisation of the leader searches)
@@ -679,6 +653,11 @@ using namespace phos;
 extern "C" phos_status phos_validate_config(uint32_t variant) {
     if (variant > 2) return fail(PHOS_EINVAL, "validate_config: variant %u", variant);
     g_val_variant = variant;
+    return PHOS_OK;
+}
+
+extern "C" phos_status phos_validate_wait_limit(uint32_t probes) {
+    g_val_wait_limit = probes;
     return PHOS_OK;
 }
 
@@ -739,6 +718,7 @@ phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
     p.nvw = nvw;
     p.stages = 0;
     p.wpb = wpb;
+    p.wait_limit = g_val_wait_limit;
     if (rule && variant != 1 && n_rec) {
         p.rule = *rule;
         if (rule_fused) *rule_fused = true;
@@ -908,6 +888,7 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
     p.nvw = nvw;
     p.stages = 0;
     p.wpb = wpb;
+    p.wait_limit = kWaitLimit;
     k_noalloc_clear<<<1, 256, 0, s>>>(sc, nvw);
     count_launch();
     PHOS_CUDA(cudaGetLastError());

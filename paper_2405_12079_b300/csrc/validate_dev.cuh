@@ -80,11 +80,76 @@ struct Acc {
 // step (batch_pairs, or the validation kernel's cross-batch stream).
 constexpr uint32_t kBatch = 1024;   // records of a full 32-word batch
 
-struct Lead {
-    uint64_t b, l;     // base and limit of word j's leader interval
-    int32_t i;         // its table index, -1 if none
-    uint32_t pm;       // its permission byte
+// The leader of a word, folded with its permission into one test: a record
+// rec (store bit 63, address bits 0..56, reserved bits 57..62) lies in the
+// leader's buffer with an admitted access iff
+//     ((rec - kb) & (km:0xffffffff)) < kl.
+// With base b and limit l (valid start offsets of a w-byte access):
+//   R and W  kb = b, km = 0x7fffffff: the store bit drops out of the
+//            difference, so loads and stores in range pass
+//   R only   kb = b, km = ~0: a store's difference is >= 2^63 > l
+//   W only   kb = b | 2^63, km = ~0: a load's difference is >= 2^63
+//   neither, or no leader: kl = 0
+// An address below b wraps to >= 2^63 - 2^57 > l either way; reserved
+// bits make the difference >= 2^57 > l (b + l <= 2^57 for any table).
+struct __align__(16) Lead {
+    uint64_t kb, kl;
+    uint32_t km;
+    int32_t i;         // leader's table index, -1 if none
+    uint64_t pad;
 };
+
+__device__ __forceinline__ bool lead_ok(const Lead &ld, uint64_t rec) {
+    const uint64_t m = ((uint64_t)ld.km << 32) | 0xffffffffull;
+    return ((rec - ld.kb) & m) < ld.kl;
+}
+
+// Lead of table entry i (or of no entry, i < 0).
+__device__ __forceinline__ Lead make_lead(const Look &L, int i, bool smem_lim) {
+    Lead ld;
+    ld.kb = 0;
+    ld.kl = 0;
+    ld.km = 0xffffffffu;
+    ld.i = i;
+    ld.pad = 0;
+    if (i >= 0) {
+        const uint64_t b = L.base[i];
+        const uint32_t pm = L.perm[i] & 3u;
+        ld.kb = pm == 2u ? (b | PHOS_REC_STORE) : b;
+        ld.kl = pm ? L.limit(i, smem_lim) : 0;
+        ld.km = pm == 3u ? 0x7fffffffu : 0xffffffffu;
+    }
+    return ld;
+}
+
+// Full classification of one record: the interval of its word's leader
+// (table entry ld.i) when the address lies in it, else the lane's own
+// search.  hit: the access lies inside some buffer; bi, pm: that buffer
+// and its permission; bad: a reserved bit is set.
+template <bool kSmemTable>
+__device__ __forceinline__ void classify(const Look &L, uint64_t rec, const Lead &ld, bool &hit,
+                                         int &bi, uint32_t &pm, bool &bad) {
+    const uint64_t a = rec & ~PHOS_REC_STORE;
+    hit = false;
+    bi = -1;
+    pm = 0;
+    bad = false;
+    if (ld.i >= 0 && (a - L.base[ld.i]) < L.limit(ld.i, kSmemTable)) {
+        hit = true;
+        bi = ld.i;
+        pm = L.perm[ld.i];
+        return;
+    }
+    bad = a > PHOS_REC_ADDR_MASK;
+    if (!bad) {
+        const int ii = L.lane_search(a);
+        if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
+            hit = true;
+            bi = ii;
+            pm = L.perm[ii];
+        }
+    }
+}
 
 // Classify one record against its word's leader interval.  The store bit
 // is cleared but the reserved bits are kept, so a malformed record lies
@@ -95,40 +160,30 @@ __device__ __forceinline__ void one_word(const Look &L, uint64_t rec, bool valid
                                          uint32_t lane, const Lead &ld, uint32_t &myvw,
                                          uint32_t *sv, uint32_t *svs, Acc &acc) {
     if (kFull) valid = true;
-    const uint64_t a = rec & ~PHOS_REC_STORE;
     const uint32_t st = (uint32_t)(rec >> 63);
-    bool hit = valid && (a - ld.b) < ld.l;
-    int bi = ld.i;
-    uint32_t pm = ld.pm;
-    const bool miss = valid && !hit;
-    bool bad = false;
-    if (__ballot_sync(0xffffffffu, miss)) {
-        if (miss) {
-            bad = a > PHOS_REC_ADDR_MASK;
-            if (!bad) {
-                const int ii = L.lane_search(a);
-                if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
-                    hit = true;
-                    bi = ii;
-                    pm = L.perm[ii];
-                }
+    bool viol = false, hit = true, bad = false;
+    const bool slow = valid && !lead_ok(ld, rec);
+    if (__ballot_sync(0xffffffffu, slow)) {
+        if (slow) {
+            int bi;
+            uint32_t pm;
+            classify<kSmemTable>(L, rec, ld, hit, bi, pm, bad);
+            viol = !(hit && ((pm >> st) & 1u));
+            if (viol && hit) {
+                atomicOr(&sv[bi >> 5], 1u << (bi & 31));
+                if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
             }
         }
     }
-    const bool viol = valid && !(hit && ((pm >> st) & 1u));
     const uint32_t vw = __ballot_sync(0xffffffffu, viol);
     myvw = (lane == j) ? vw : myvw;
     if (vw) {
         const uint32_t sw = __ballot_sync(0xffffffffu, viol && st);
-        const uint32_t uw = __ballot_sync(0xffffffffu, valid && !hit);
+        const uint32_t uw = __ballot_sync(0xffffffffu, viol && !hit);
         if (lane == 0) {
             acc.c0 += __popc(vw);
             acc.c1 += __popc(sw);
             acc.c2 += __popc(uw);
-        }
-        if (viol && hit) {
-            atomicOr(&sv[bi >> 5], 1u << (bi & 31));
-            if (st) atomicOr(&svs[bi >> 5], 1u << (bi & 31));
         }
         acc.bad |= bad;
     }
@@ -179,29 +234,16 @@ __device__ __forceinline__ uint32_t spread16(uint32_t x) {
     return x;
 }
 
-// General path of one record of a pair (a lane's element e): interval of
-// the word's leader, else the lane's own search; victims marked here.
+// General path of one record of a pair (a lane's element e); victims are
+// marked here.
 template <bool kSmemTable>
 __device__ __forceinline__ bool pair_record(const Look &L, uint64_t rec, const Lead &ld,
                                             uint32_t *sv, uint32_t *svs, bool &hit,
                                             bool &bad) {
-    const uint64_t a = rec & ~PHOS_REC_STORE;
     const uint32_t st = (uint32_t)(rec >> 63);
-    hit = (a - ld.b) < ld.l;
-    int bi = ld.i;
-    uint32_t pm = ld.pm;
-    bad = false;
-    if (!hit) {
-        bad = a > PHOS_REC_ADDR_MASK;
-        if (!bad) {
-            const int ii = L.lane_search(a);
-            if (ii >= 0 && (a - L.base[ii]) < L.limit(ii, kSmemTable)) {
-                hit = true;
-                bi = ii;
-                pm = L.perm[ii];
-            }
-        }
-    }
+    int bi;
+    uint32_t pm;
+    classify<kSmemTable>(L, rec, ld, hit, bi, pm, bad);
     const bool viol = !(hit && ((pm >> st) & 1u));
     if (viol && hit) {
         atomicOr(&sv[bi >> 5], 1u << (bi & 31));
@@ -217,9 +259,7 @@ __device__ __forceinline__ void pair_step(const Look &L, ulonglong2 x, const Lea
                                           uint32_t q, uint32_t lane, uint32_t *sv,
                                           uint32_t *svs, Acc &acc, uint32_t &myvw) {
     const uint64_t x0 = x.x, x1 = x.y;
-    const uint64_t a0 = x0 & ~PHOS_REC_STORE, a1 = x1 & ~PHOS_REC_STORE;
-    const bool ok0 = (a0 - ld.b) < ld.l && ((ld.pm >> (uint32_t)(x0 >> 63)) & 1u);
-    const bool ok1 = (a1 - ld.b) < ld.l && ((ld.pm >> (uint32_t)(x1 >> 63)) & 1u);
+    const bool ok0 = lead_ok(ld, x0), ok1 = lead_ok(ld, x1);
     if (__ballot_sync(0xffffffffu, !(ok0 && ok1))) {
         bool h0, h1, bad0, bad1;
         const bool v0 = pair_record<kSmemTable>(L, x0, ld, sv, svs, h0, bad0);

@@ -101,6 +101,62 @@ def bench_validate(K, out, variants=(1, 2)):
     phos.validate_config(0)
 
 
+def bench_validate_distinct(K, out, reps=5):
+    """Validation over K distinct training-kernel traces (each kernel its
+    own read/write sets, as the benchmark's 200 kernels) in one launch, with
+    the union of their speculated sets, next to the first 50 of them, next
+    to K copies of the first trace with that trace's own speculated set."""
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(n_kernels=K)
+    lay, rng = cfg["layout"], cfg["rng"]
+    t = phos.Table(lay.base(VA0), lay.size)
+    ks = wl.make_training_kernels(rng, lay, VA0, K, 1_300_000, 0.001)
+    perms = []
+    for k in ks:
+        p = np.zeros(lay.n, np.uint8)
+        p[k.reads] = phos.PERM_R
+        p[k.writes] = phos.PERM_RW
+        perms.append(p)
+    n1 = len(ks[0].trace)
+    big = torch.from_numpy(np.concatenate([k.trace for k in ks]).view(np.uint8)).cuda()
+    tiled = torch.from_numpy(np.tile(ks[0].trace, K).view(np.uint8)).cuda()
+    u_all = torch.from_numpy(np.maximum.reduce(perms)).cuda()
+    u_50 = torch.from_numpy(np.maximum.reduce(perms[:50])).cuda()
+    p0 = torch.from_numpy(perms[0]).cuda()
+    N = n1 * K
+    bm = torch.empty(((N + 31) // 32) * 4, dtype=torch.uint8, device="cuda")
+    cnt = torch.empty(24, dtype=torch.uint8, device="cuda")
+    vv = torch.empty(256, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def run(perm, ptr, nrec):
+        phos.validate(t, perm.data_ptr(), ptr, nrec, 4, bm.data_ptr(), cnt.data_ptr(),
+                      vv.data_ptr(), vv.data_ptr() + 128, None, 0, st.data_ptr(), s)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()                            # L2 flush (2 x L2)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts)), float(np.min(ts))
+
+    for name, perm, ptr, nrec in (("distinct_all", u_all, big.data_ptr(), N),
+                                  ("distinct_50", u_50, big.data_ptr(), n1 * min(50, K)),
+                                  ("tiled_one", p0, tiled.data_ptr(), N)):
+        med, best = timed(lambda: run(perm, ptr, nrec))
+        out["validate_" + name] = dict(records=nrec, ms_median=med, ms_best=best,
+                                       grec_s=nrec / med / 1e6, gbs=nrec * 8.125 / med / 1e6,
+                                       violations=int(cnt.cpu().numpy().view(np.uint64)[0]))
+
+
 def bench_copy(gb, out):
     s = torch.cuda.current_stream().cuda_stream
     G = int(gb) << 30
@@ -197,7 +253,8 @@ def bench_speculate(out, n_launch=20000):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--kernel", default="all", choices=["validate", "copy", "speculate", "all"])
+    ap.add_argument("--kernel", default="all",
+                    choices=["validate", "validate_distinct", "copy", "speculate", "all"])
     ap.add_argument("--traces", type=int, default=160)
     ap.add_argument("--copy-gb", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0, help="validate kernel variant (0 = both)")
@@ -205,6 +262,8 @@ def main():
     out = {}
     if a.kernel in ("validate", "all"):
         bench_validate(a.traces, out, (1, 2) if a.variant == 0 else (a.variant,))
+    if a.kernel == "validate_distinct":
+        bench_validate_distinct(a.traces, out)
     if a.kernel in ("copy", "all"):
         bench_copy(a.copy_gb, out)
     if a.kernel in ("speculate", "all"):

@@ -49,6 +49,7 @@ _SIGS = {
     "phos_copy_config": (_i32, [_u64, _u32]),
     "phos_validate_config": (_i32, [_u32]),
     "phos_validate_grid": (_i32, [_u32]),
+    "phos_validate_wait_limit": (_i32, [_u32]),
     "phos_host_copy_config": (_i32, [_u64]),
     "phos_ckpt_frequency": (_i32, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
                                    _c.c_double, _P(_c.c_double), _P(_c.c_double)]),
@@ -71,6 +72,7 @@ _SIGS = {
     "phos_server_start": (_i32, [_vp, _P(_vp)]),
     "phos_server_submit": (_i32, [_vp, _vp, _P(_u64)]),
     "phos_server_poll": (_i32, [_vp, _u64, _vp]),
+    "phos_server_cancel": (_i32, [_vp, _u64]),
     "phos_server_drain": (_i32, [_vp, _u32]),
     "phos_server_stop": (_i32, [_vp]),
     "phos_speculate_device": (_i32, [_vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp]),
@@ -111,7 +113,7 @@ class ServerDesc(_c.Structure):
 
 class ServerStats(_c.Structure):
     _fields_ = [("app_copies", _u64), ("app_bytes", _u64), ("paused_turns", _u64),
-                ("batches", _u64)]
+                ("batches", _u64), ("cancelled", _u64)]
 
 
 class Request(_c.Structure):
@@ -333,6 +335,10 @@ def ckpt_frequency(n_gpus, fail_per_hour, overhead_h, restore_h, hours):
 
 def validate_grid(ctas=0):
     return check(lib().phos_validate_grid(ctas), "validate_grid")
+
+
+def validate_wait_limit(probes=1 << 24):
+    return check(lib().phos_validate_wait_limit(probes), "validate_wait_limit")
 
 
 def host_copy_config(dma_min_bytes=0):
@@ -568,6 +574,9 @@ class Server:
         r = Result()
         check(lib().phos_server_poll(self.h, ticket, _c.byref(r)), "server_poll")
         return {f: getattr(r, f) for f, _ in r._fields_}
+
+    def cancel(self, ticket):
+        check(lib().phos_server_cancel(self.h, ticket), "server_cancel")
 
     def drain(self, timeout_ms=600_000):
         check(lib().phos_server_drain(self.h, timeout_ms), "server_drain")

@@ -55,9 +55,11 @@ class World:
         self.host.copy_(torch.from_numpy(self.host_h))
         torch.cuda.synchronize()
 
-    def expected(self):
+    def expected(self, skip=()):
         dev, host = self.dev_h.copy(), self.host_h.copy()
-        for r in self.reqs:
+        for q, r in enumerate(self.reqs):
+            if q in skip:
+                continue
             lay, n = r["lay"], r["lay"].n
             d = np.zeros(n, copyeng.DESC_DTYPE)
             for i in range(n):
@@ -226,3 +228,54 @@ def test_app_copy_rejects_pageable_and_same_side():
         assert e.value.code == phos.PHOS_EINVAL
     assert srv.stats()["app_copies"] == 0
     srv.close()
+
+
+def test_cancelled_requests_leave_the_others_exact():
+    """Cancellation (a failure the serving loop must survive): one admitted
+    checkpoint, one admitted restore and one queued request are cancelled
+    while a pending application transfer holds every host leg back, so none
+    of their pieces has been issued.  They end as cancelled, their images
+    and buffers are untouched, the staging of the cancelled checkpoint is
+    released, and every other request's bytes are exactly the oracle's."""
+    w = World(9, n_req=10)
+    cks = [a256(r["img"]) for r in w.reqs if r["kind"] == phos.REQ_CHECKPOINT]
+    staging = torch.empty(sum(cks), dtype=torch.uint8, device="cuda")
+    src = torch.zeros(1 << 20, dtype=torch.uint8).pin_memory()
+    dev = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    w.reset()
+    srv = phos.Server(4, staging.data_ptr(), staging.numel(), chunk=64 << 10, dma_min=256 << 10,
+                      app_priority=True, window=1 << 20)
+    app = torch.cuda.Stream()
+    with torch.cuda.stream(app):
+        torch.cuda._sleep(200_000_000)          # >= 98 ms at 2032 MHz
+    srv.app_copy(dev.data_ptr(), src.data_ptr(), src.numel(), app.cuda_stream)
+    tks = [w.submit(srv, r) for r in w.reqs]
+    # requests 0 (checkpoint) and 1 (restore) are admitted, 9 is queued
+    t_end = time.time() + 1.0
+    while time.time() < t_end and not (srv.poll(tks[0])["state"] == 1 and
+                                       srv.poll(tks[1])["state"] == 1):
+        time.sleep(0.0005)
+    states = [srv.poll(t)["state"] for t in tks]
+    cancel = (0, 1, 9)
+    for q in cancel:
+        srv.cancel(tks[q])
+    assert states[9] == 0 and srv.poll(tks[9])["state"] == 4
+    srv.drain(60_000)
+    app.synchronize()
+    res = [srv.poll(t) for t in tks]
+    st = srv.stats()
+    srv.close()
+    torch.cuda.synchronize()
+    assert states[0] == 1 and states[1] == 1
+    for q, x in enumerate(res):
+        assert x["state"] == (4 if q in cancel else 2) and x["status"] == 0
+    assert st["cancelled"] == 3
+    exp_dev, exp_host = w.expected(skip=cancel)
+    assert np.array_equal(w.dev.cpu().numpy(), exp_dev)
+    assert np.array_equal(w.host.numpy(), exp_host)
+    with pytest.raises(phos.PhosError):
+        srv2 = phos.Server(1, staging.data_ptr(), staging.numel())
+        try:
+            srv2.cancel(12345)
+        finally:
+            srv2.close()

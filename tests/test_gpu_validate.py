@@ -172,3 +172,28 @@ def test_large_traces_take_the_wide_batches(n_rec):
     perm[writes] = phos.PERM_RW
     rec, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, n_rec, 0.002, 0.3)
     check(t, base, lay.size, perm, rec, 4, idx_cap=20_000)
+
+
+def test_ring_wait_that_runs_out_reports_etimedout(variant):
+    """A bounded device wait that runs out (the ring variant's tile waits,
+    limited to zero probes) stops the kernel with PHOS_ETIMEDOUT in its
+    status word after its copies in flight have landed; the device stays
+    usable and the next launch is exact again.  No fault, trap or hang."""
+    if variant != 1:
+        pytest.skip("the bounded tile waits belong to the ring variant")
+    cfg = wl.training(n_kernels=1)
+    lay, rng = cfg["layout"], cfg["rng"]
+    base = lay.base(VA0)
+    t = phos.Table(base, lay.size)
+    reads, writes = wl.pick_sets(rng, lay.n)
+    perm = np.zeros(lay.n, np.uint8)
+    perm[reads] = phos.PERM_R
+    perm[writes] = phos.PERM_RW
+    rec, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, 1_300_000, 0.001, 0.0)
+    phos.validate_wait_limit(0)
+    try:
+        got = run_validate(t, perm, rec, 4)
+    finally:
+        phos.validate_wait_limit()
+    assert got["status"] == phos.PHOS_ETIMEDOUT
+    check(t, base, lay.size, perm, rec, 4)
