@@ -254,6 +254,7 @@ class Marks:
 
 
 def run_gpu(args, rank, world):
+    """The headline step; returns rank 0's JSON line (None elsewhere)."""
     import torch
     import torch.distributed as dist
     from paper_2405_12079_b300 import build as B
@@ -284,47 +285,17 @@ def run_gpu(args, rank, world):
 
     marks = Marks(torch)
 
+    ns = {"sync": 0, "nosync": phos.CKPT_NO_SYNC, "concurrent": phos.CKPT_CONCURRENT}[args.rounds]
+
     def hook_run(mode, max_passes=0, times=None):
-        # lockstep round with phase marks (same calls as runner.DeviceProcess);
-        # max_passes > 0: iterative recopy, another concurrent pass while the
-        # dirty bytes shrink
-        ns = {"sync": 0, "nosync": phos.CKPT_NO_SYNC,
-              "concurrent": phos.CKPT_CONCURRENT}[args.rounds]
-        c = (phos.Checkpoint(dp.table, phos.CKPT_COW | ns, image.data_ptr(), image.numel(),
-                             chunk, 4, staging.data_ptr(), staging_bytes, s) if mode == "cow" else
-             phos.Checkpoint(dp.table, phos.CKPT_RECOPY | ns, image.data_ptr(), image.numel(),
-                             chunk, 4, None, 0, s))
-        k, prev, passes = 0, None, 0
-        while k < len(dp.kernels):
-            marks.mark("copier")
-            if c.advance(quota):
-                db = dp.dirty_bytes(c) if max_passes else 0
-                if passes < max_passes and db > 0 and (prev is None or db < prev):
-                    c.begin_pass()
-                    prev, passes = db, passes + 1
-                else:
-                    break
-            pk = dp.kernels[k]
-            marks.mark("cow" if mode == "cow" else "dirty_marking")
-            c.before_kernel(pk.speculate(dp.table, dp.perm))
-            marks.mark("app_kernel")
-            dp.run_kernel(k)
-            marks.mark("validate")
-            mis = c.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
-            k += 1
-            if mis:
-                break
-        marks.mark("finish")
-        if times is not None:
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-        c.finish()
-        if times is not None:
-            times.append(time.perf_counter() - t)
-        marks.mark("end")
-        st = c.stats()
-        c.close()
-        return st
+        # the session rounds of runner.DeviceProcess, with phase marks;
+        # max_passes > 0: iterative recopy, another concurrent pass while
+        # the dirty bytes shrink
+        if mode == "cow":
+            return dp._ckpt(phos.CKPT_COW | ns, image, quota, chunk, staging, staging_bytes,
+                            mark=marks.mark, finish_times=times, logs=False)
+        return dp._ckpt(phos.CKPT_RECOPY | ns, image, quota, chunk, None, 0, max_passes, 0,
+                        mark=marks.mark, finish_times=times, logs=False)
 
     def step():
         a = hook_run("cow")
@@ -441,7 +412,7 @@ def run_gpu(args, rank, world):
     # launch over 50 traces back to back (the batched shape)
     nvw = (lay.n + 31) // 32
     maxw = max((p.n_rec + 31) // 32 for p in dp.kernels)
-    bm = torch.empty(4 * maxw * 50, dtype=torch.uint8, device="cuda")
+    bm = torch.empty(4 * maxw * len(dp.kernels), dtype=torch.uint8, device="cuda")
     cnt = torch.empty(24, dtype=torch.uint8, device="cuda")
     vv = torch.empty(8 * nvw, dtype=torch.uint8, device="cuda")
     stw = torch.zeros(4, dtype=torch.uint8, device="cuda")
@@ -479,6 +450,20 @@ def run_gpu(args, rank, world):
                                          vv.data_ptr() + 4 * nvw, None, 0, stw.data_ptr(), s))
     cat_gbs = cat_n * 8.125 / (cat_ms * 1e6)
     del cat
+    # one launch over all 200 distinct traces (260M records, 2.1 GB, 16x L2),
+    # L2 flushed before each repetition
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    all_tr = torch.cat([p.d_trace for p in dp.kernels])
+    all_n = all_tr.numel() // 8
+    aperm = torch.stack(perms).max(dim=0).values.contiguous()
+    all_ms = 1e30
+    for _ in range(3):
+        flush.zero_()
+        all_ms = min(all_ms, ev_ms(lambda: phos.validate(
+            dp.table, aperm.data_ptr(), all_tr.data_ptr(), all_n, 4, bm.data_ptr(), cnt.data_ptr(),
+            vv.data_ptr(), vv.data_ptr() + 4 * nvw, None, 0, stw.data_ptr(), s), reps=1))
+    all_gbs = all_n * 8.125 / (all_ms * 1e6)
+    del all_tr, flush
     # CoW copy kernel alone: the step's largest buffers live -> staging
     order = np.argsort(-lay.size.astype(np.int64))
     rows, off = [], 0
@@ -497,7 +482,7 @@ def run_gpu(args, rank, world):
     # (host->device inside the timed region) and its stats are read back
     h_tr = [p.d_trace.cpu().pin_memory() for p in dp.kernels]
     h2d = sum(t.numel() for t in h_tr)
-    e_steps = max(1, min(2, args.steps))
+    e_steps = args.steps
     torch.cuda.synchronize()
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     x0.record()
@@ -563,6 +548,11 @@ def run_gpu(args, rank, world):
                  "traffic_source": "profiles/validate_b_training_trace_208M.md (ncu DRAM bytes "
                                    "of 208M records), scaled by records",
                  "accesses_per_s": cat_n / (cat_ms * 1e-3), "launch_us": 1e3 * cat_ms},
+                {"kernel": "k_validate_b, one launch over all 200 distinct traces (260M "
+                           "records, 2.1 GB, union of their speculated sets, L2 flushed)",
+                 "bound": "hbm", "achieved": all_gbs, "peak": hbm, "unit": "GB/s",
+                 "frac": all_gbs / hbm, "traffic": None,
+                 "accesses_per_s": all_n / (all_ms * 1e-3), "launch_us": 1e3 * all_ms},
                 {"kernel": "k_copy_main, CoW live -> staging (%d buffers, %.2f GB)"
                            % (len(rows), off / 1e9),
                  "bound": "hbm", "achieved": d2d_gbs, "peak": hbm, "unit": "GB/s",
@@ -583,7 +573,8 @@ def run_gpu(args, rank, world):
             "clocks": clocks,
             "setup_s": setup_s,
         }
-        print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 BATCHED = ("batched: 64 independent process images, 20-2,000 buffers each (log-uniform), "
@@ -630,7 +621,7 @@ def oracle_batched_sample():
                       "single thread" % (nbuf, tv, tc)}
 
 
-def run_batched(args, rank, world):
+def batched_line(args, world):
     """Batched form: all images' validation and copies in one graph launch."""
     import torch
     from paper_2405_12079_b300 import phos, workloads as wl
@@ -738,10 +729,15 @@ def run_batched(args, rank, world):
                                            "scaled to this launch",
                          "algorithmic_bytes": alg},
             "status": info["status"], "gpu_launches": launches, "clocks": clocks}
+    plan.close()
+    return line
+
+
+def run_batched(args, rank, world):
+    line = batched_line(args, world)
     if rank == 0:
         line["cpu_baseline"] = oracle_batched_sample()
         print(json.dumps(line), flush=True)
-    plan.close()
 
 
 SERVING = ("serving loop: Poisson checkpoint/restore requests (1:1) at 50 req/s for a "
@@ -751,9 +747,9 @@ SERVING = ("serving loop: Poisson checkpoint/restore requests (1:1) at 50 req/s 
            "directions at once) vs one request at a time")
 
 
-def run_serving(args, rank, world):
+def serving_line(args, world, window=None):
     """Request loop: p50/p99 latency and GB/s, continuous batching vs one at
-    a time, on the same arrival sequence."""
+    a time, on the same arrival sequence (window: arrival window in s)."""
     import threading
     import torch
     from paper_2405_12079_b300 import phos, workloads as wl
@@ -761,7 +757,8 @@ def run_serving(args, rank, world):
     torch.cuda.set_device(dev)
     s = torch.cuda.current_stream().cuda_stream
     sc = args.scale
-    window = 30.0 * min(1.0, max(sc, 0.1))
+    if window is None:
+        window = 30.0 * min(1.0, max(sc, 0.1))
     cfg = wl.serving(window_s=window, scale=sc)
     rng = cfg["rng"]
     reqs = cfg["requests"]
@@ -853,6 +850,11 @@ def run_serving(args, rank, world):
             "p99_speedup_vs_one_at_a_time": alone["p99_ms"] / cont["p99_ms"],
             "gbs_speedup_vs_one_at_a_time": cont["gbs_total"] / alone["gbs_total"],
             "gpu_launches": launches, "clocks": clocks}
+    return line
+
+
+def run_serving(args, rank, world):
+    line = serving_line(args, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -864,7 +866,21 @@ RESTORE = ("large on-demand restore: 10,000 buffers log-normal 4 KB-2 GB, %.0f G
            "before each kernel) vs stop-the-world restore then the same replay")
 
 
-def run_restore(args, rank, world):
+def stall_split(stalls, od):
+    """Stall percentiles of the kernels that waited for on-demand copies and
+    of those that did not."""
+    od = np.asarray(od)[:len(stalls)]
+    out = {}
+    for name, m in (("with_ondemand", od > 0), ("without_ondemand", od == 0)):
+        x = stalls[:len(od)][m]
+        out[name] = ({"kernels": int(m.sum()), "p50_ms": float(np.percentile(x, 50)),
+                      "p99_ms": float(np.percentile(x, 99)),
+                      "ondemand_mb_mean": float(od[m].mean() / 1e6)} if len(x) else
+                     {"kernels": 0})
+    return out
+
+
+def restore_line(args, world):
     import torch
     from paper_2405_12079_b300 import phos, runner, workloads as wl
     dev = int(os.environ.get("LOCAL_RANK", 0))
@@ -952,8 +968,16 @@ def run_restore(args, rank, world):
         b.record()
         torch.cuda.synchronize()
         st = r.stats()
+        od = r.log(0)
         r.close()
         stalls = np.array([x.elapsed_time(y) for x, y in evs]) if evs else np.zeros(1)
+        # on-demand bytes each kernel waited for (rounds of the on-demand log)
+        od_k = np.zeros(max(len(evs), 1))
+        for row in od:
+            if int(row[0]) < len(od_k):
+                od_k[int(row[0])] += float(row[3])
+        st = dict(st)
+        st["od_per_kernel"] = od_k
         first_ms = a.elapsed_time(evs[0][1]) if evs else 0.0
         total = a.elapsed_time(b)
         phos.harness_digest(ptrs, lens, dig.data_ptr(), s)
@@ -978,6 +1002,7 @@ def run_restore(args, rank, world):
             "concurrent": {"total_ms": total, "first_kernel_ms": first_ms,
                            "stall_p50_ms": float(np.percentile(stalls, 50)),
                            "stall_p99_ms": float(np.percentile(stalls, 99)),
+                           "stall_split": stall_split(stalls, st["od_per_kernel"]),
                            "kernels_during_restore": during,
                            "ondemand_bytes": st["ondemand_bytes"],
                            "copier_bytes": st["copier_bytes"],
@@ -992,7 +1017,48 @@ def run_restore(args, rank, world):
             "verified": {"final_memory_equals_stw_restore_plus_replay":
                          bool(torch.equal(dig_stw, dig_cc)) and bool(torch.equal(dig_stw, lock[5]))},
             "gpu_launches": launches, "clocks": clocks}
+    return line
+
+
+def run_restore(args, rank, world):
+    line = restore_line(args, world)
     if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def release_memory():
+    """Free what an arm left in torch's device and pinned-host caches."""
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    torch._C._host_emptyCache()
+
+
+def run_default(args, rank, world):
+    """The headline training step, then the batched, serving and restore
+    forms measured in the same run (outside the step's timed region), each
+    with its own clocks record; rank 0 prints one line."""
+    import copy
+    line = run_gpu(args, rank, world)
+    release_memory()
+    arms = {}
+    if not args.headline_only:
+        for name, fn in (("batched", lambda a: batched_line(a, world)),
+                         ("serving", lambda a: serving_line(a, world, window=args.serving_window)),
+                         ("restore", lambda a: restore_line(a, world))):
+            a = copy.copy(args)
+            a.steps, a.warmup = 5, 3
+            try:
+                arms[name] = fn(a)
+            except Exception as e:              # an arm that fails is reported, not fatal
+                arms[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+            release_memory()
+    if rank == 0 and line is not None:
+        if arms:
+            line["arms"] = arms
+            line["gpu_launches_arms"] = sum(int(x.get("gpu_launches", 0)) for x in arms.values())
         print(json.dumps(line), flush=True)
 
 
@@ -1327,6 +1393,10 @@ def main():
                          "rule); concurrent: also the copier on its own stream")
     ap.add_argument("--server-window", type=int, default=0,
                     help="serving: host-leg MiB queued per direction (0 = two 64 MiB batches)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="default workload: skip the batched, serving and restore arms")
+    ap.add_argument("--serving-window", type=float, default=10.0,
+                    help="default workload: arrival window (s) of its serving arm")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload (parity / quick runs); 1.0 = the full 40 GB")
     args = ap.parse_args()
@@ -1354,7 +1424,7 @@ def main():
     elif args.workload == "rounds":
         run_rounds(args, rank, world)
     else:
-        run_gpu(args, rank, world)
+        run_default(args, rank, world)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

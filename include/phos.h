@@ -575,6 +575,17 @@ typedef struct {
     uint64_t image_bytes;
     uint32_t *d_present;     /* optional device u32[ceil(n/32)] kept in step
                                 with the restored set (zeroed by begin)      */
+    const uint64_t *d_manifest; /* optional device u64[n], the image's
+                                manifest (phos_image_manifest): each buffer
+                                is digested on the device as soon as its
+                                last byte lands, before any kernel can use
+                                it; a mismatch sets PHOS_ECORRUPT, which
+                                the next call that synchronises returns
+                                (an after_kernel of lockstep rounds, else
+                                finish; stats.corrupt_buf names the lowest
+                                damaged buffer found).  With a manifest, an
+                                image shorter than phos_image_bytes is
+                                PHOS_ECORRUPT at begin.                     */
 } phos_restore_desc_t;
 
 typedef struct {
@@ -585,8 +596,19 @@ typedef struct {
     uint64_t violations;
     int64_t misspec_round;
     uint32_t done;           /* every buffer present                         */
-    uint32_t reserved;
+    int32_t corrupt_buf;     /* lowest buffer found whose restored bytes
+                                did not match the manifest, -1 if none (or
+                                no manifest)                                */
 } phos_restore_stats_t;
+
+/* Manifest of a checkpoint image: d_digest[i] (device u64[n], overwritten)
+ * = the digest of buffer i's bytes in the image (the definition in
+ * phos_harness.h), for a later restore to verify against.  image: pinned
+ * host (read through its mapped address, one pass over PCIe) or device.
+ * PHOS_ECORRUPT if image_bytes is shorter than phos_image_bytes(t).
+ * Asynchronous on stream. */
+phos_status phos_image_manifest(const phos_table_t *t, const void *image, uint64_t image_bytes,
+                                uint64_t *d_digest, phos_stream_t stream);
 
 /* Concurrent restore (Sec. 6): nothing is present at begin. */
 phos_status phos_restore_begin(const phos_table_t *t, const phos_restore_desc_t *d,

@@ -18,6 +18,7 @@
 // a validation result, so the host can run ahead of the device; it learns
 // of a CoW mis-speculation from the mapped word at its next call, and at
 // the latest at finish, which then copies every buffer stop-the-world.
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -151,7 +152,7 @@ struct Session {
     int64_t *h_flag = nullptr, *d_flag = nullptr;
     // concurrent sessions: the copier's own stream, a clone of the table
     // (its own copy-engine scratch), one event per copier batch (ring)
-    static constexpr uint32_t kRing = 64;
+    static constexpr uint32_t kRing = 1024;
     cudaStream_t cs = nullptr;
     phos_table_t *tc = nullptr;
     cudaEvent_t app_ev = nullptr;
@@ -929,6 +930,26 @@ struct phos_restore {
     int64_t misspec = -1;
     bool in_kernel = false;
     uint64_t waited = 0;     // concurrent: latest copier batch the caller's stream waited for
+    // integrity check: manifest digests, per-buffer accumulators and tile
+    // counters, the lowest corrupt buffer (mapped host word)
+    const uint64_t *d_manifest = nullptr;
+    unsigned long long *d_vacc = nullptr;
+    uint32_t *d_vcnt = nullptr;
+    int *h_bad = nullptr, *d_bad = nullptr;
+
+    // Verify the buffers whose last byte was just copied, on the stream of
+    // that copy (before any kernel can use them).
+    phos_status verify(const std::vector<uint32_t> &bufs, cudaStream_t st) {
+        if (!d_manifest || bufs.empty()) return PHOS_OK;
+        return verify_buffers(ss.t, bufs, d_manifest, d_vacc, d_vcnt, ss.d_status, d_bad, st);
+    }
+
+    ~phos_restore() {
+        ss.sync_streams();
+        if (d_vacc) cudaFree(d_vacc);
+        if (d_vcnt) cudaFree(d_vcnt);
+        if (h_bad) cudaFreeHost(h_bad);
+    }
 
     bool all_present() const {
         for (uint8_t p : present)
@@ -943,6 +964,9 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
     *out = nullptr;
     if (d->access_bytes == 0 || d->chunk == 0 || d->chunk % 256)
         return fail(PHOS_EINVAL, "restore_begin: access_bytes >= 1, chunk a multiple of 256");
+    if (d->d_manifest && d->image && d->image_bytes < t->image_bytes)
+        return fail(PHOS_ECORRUPT, "restore_begin: image truncated (%llu of %llu bytes)",
+                    (unsigned long long)d->image_bytes, (unsigned long long)t->image_bytes);
     if (!d->image || d->image_bytes < t->image_bytes)
         return fail(PHOS_EINVAL, "restore_begin: image smaller than %llu bytes",
                     (unsigned long long)t->image_bytes);
@@ -959,6 +983,21 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
     r->image = d->image;
     r->image_bytes = d->image_bytes;
     r->d_present = d->d_present;
+    if (d->d_manifest) {
+        cudaError_t ce;
+        const size_t nn = std::max(t->n, 1u);
+        if ((ce = cudaMalloc(&r->d_vacc, 8 * nn)) != cudaSuccess ||
+            (ce = cudaMalloc(&r->d_vcnt, 4 * nn)) != cudaSuccess ||
+            (ce = cudaMemset(r->d_vacc, 0, 8 * nn)) != cudaSuccess ||
+            (ce = cudaMemset(r->d_vcnt, 0, 4 * nn)) != cudaSuccess ||
+            (ce = cudaHostAlloc(&r->h_bad, 64, cudaHostAllocMapped)) != cudaSuccess ||
+            (ce = cudaHostGetDevicePointer((void **)&r->d_bad, r->h_bad, 0)) != cudaSuccess) {
+            delete r;
+            return cuda_fail(ce, "restore_begin: integrity scratch");
+        }
+        *(volatile int *)r->h_bad = INT_MAX;
+        r->d_manifest = d->d_manifest;
+    }
     r->present.assign(t->n, 0);
     r->before.assign(t->n, 0);
     if (r->d_present && t->n) {
@@ -973,15 +1012,42 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
     return PHOS_OK;
 }
 
+// With the copier on its own stream a round's pieces go out in sub-batches
+// of about this many bytes, each closed at a buffer's last piece and
+// followed by its own event, so a kernel waits only for the sub-batch that
+// lands its buffers, not for the whole round's quota.
+constexpr uint64_t kSubBatch = 16ull << 20;
+
 static phos_status restore_advance(phos_restore *R, uint64_t quota) {
     Session &S = R->ss;
     const phos_table *t = S.t;
     std::vector<phos_copy_t> v;
-    const uint64_t b = S.batch + 1;
+    std::vector<uint32_t> landed, touched;
+    uint64_t b = S.batch + 1, sub_bytes = 0;
     if (S.cs) {
         PHOS_CUDA(cudaEventRecord(S.app_ev, S.s));
         PHOS_CUDA(cudaStreamWaitEvent(S.cs, S.app_ev, 0));
     }
+    phos_status err = PHOS_OK;
+    // issue the pieces gathered so far; with the copier stream, as
+    // sub-batch b with its own event
+    auto flush = [&]() -> phos_status {
+        if (v.empty()) return PHOS_OK;
+        phos_status r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present, true);
+        if (r) return r;
+        if ((r = R->verify(landed, S.cs ? S.cs : S.s))) return r;
+        if (S.cs) {
+            for (uint32_t i : touched) S.last_batch[i] = b;
+            S.batch = b;
+            PHOS_CUDA(cudaEventRecord(S.bev[b % Session::kRing], S.cs));
+            ++b;
+        }
+        v.clear();
+        landed.clear();
+        touched.clear();
+        sub_bytes = 0;
+        return PHOS_OK;
+    };
     uint64_t moved = S.advance(
         quota,
         [&](uint32_t i, uint64_t off, uint64_t len) {
@@ -991,23 +1057,22 @@ static phos_status restore_advance(phos_restore *R, uint64_t quota) {
             d.len = len;
             d.buf = i;
             d.flags = PHOS_COPY_IMAGE_TO_LIVE;
-            if (off + len == t->size[i]) {
+            const bool last = off + len == t->size[i];
+            if (last) {
                 R->present[i] = 1;
+                landed.push_back(i);
                 if (R->d_present) d.flags |= PHOS_COPY_MARK_PRESENT;
             }
             v.push_back(d);
-            if (S.cs) S.last_batch[i] = b;
+            touched.push_back(i);
+            sub_bytes += len;
+            if (S.cs && last && sub_bytes >= kSubBatch && !err) err = flush();
             return false;
         },
         [&](uint32_t i) { return R->present[i] != 0; });
     R->copier_bytes += moved;
-    phos_status r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present, true);
-    if (r) return r;
-    if (S.cs && !v.empty()) {
-        S.batch = b;
-        PHOS_CUDA(cudaEventRecord(S.bev[b % Session::kRing], S.cs));
-    }
-    return PHOS_OK;
+    if (err) return err;
+    return flush();
 }
 
 // Mis-speculation (Sec. 6): roll back to the checkpoint's state, every
@@ -1019,7 +1084,9 @@ static phos_status restore_rollback(phos_restore *R, int64_t k) {
     phos_status r = S.cs ? S.app_wait(S.batch) : PHOS_OK;
     if (r) return r;
     std::vector<phos_copy_t> v;
+    std::vector<uint32_t> all(S.n);
     for (uint32_t j = 0; j < S.n; ++j) {
+        all[j] = j;
         phos_copy_t d;
         d.src_off = S.t->img_off[j];
         d.dst_off = 0;
@@ -1031,7 +1098,9 @@ static phos_status restore_rollback(phos_restore *R, int64_t k) {
         S.state[j] = kDone;
         S.copied[j] = S.t->size[j];
     }
-    return S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
+    phos_status r2 = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
+    if (r2) return r2;
+    return R->verify(all, S.s);
 }
 
 extern "C" phos_status phos_restore_advance(phos_restore_t *R, uint64_t quota, int *done) {
@@ -1067,8 +1136,10 @@ extern "C" phos_status phos_restore_before_kernel(phos_restore_t *R, const uint8
         }
     }
     std::vector<phos_copy_t> v;
+    std::vector<uint32_t> landed;
     for (uint32_t i = 0; i < S.n; ++i) {
         if (!perm[i] || R->present[i]) continue;
+        landed.push_back(i);
         const uint64_t cp = S.copied[i], sz = t->size[i];
         phos_copy_t d;
         d.src_off = t->img_off[i] + cp;
@@ -1088,6 +1159,7 @@ extern "C" phos_status phos_restore_before_kernel(phos_restore_t *R, const uint8
         R->before[i] = R->present[i] && (!S.cs || S.last_batch[i] <= R->waited);
     r = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
     if (r) return r;
+    if ((r = R->verify(landed, S.s))) return r;
     if (S.nosync && (r = S.upload_slot(R->before))) return r;
     R->in_kernel = true;
     return PHOS_OK;
@@ -1153,6 +1225,11 @@ extern "C" phos_status phos_restore_stats(const phos_restore_t *R, phos_restore_
     o->violations = R->ss.violations;
     o->misspec_round = R->misspec;
     o->done = R->all_present() ? 1 : 0;
+    o->corrupt_buf = -1;
+    if (R->h_bad) {
+        const int b = *(volatile int *)R->h_bad;
+        if (b != INT_MAX) o->corrupt_buf = b;
+    }
     return PHOS_OK;
 }
 

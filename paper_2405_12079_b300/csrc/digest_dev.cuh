@@ -1,0 +1,55 @@
+// The order-independent 64-bit buffer digest (include/phos_harness.h):
+// D = sum over the 8-byte little-endian words j of mix64(word_j + j * GOLDEN)
+// mod 2^64, the last word zero-padded; mix64 is the SplitMix64 output
+// function (Steele, Lea & Flood, OOPSLA 2014).
+#pragma once
+#include <stdint.h>
+
+namespace phos {
+
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t sm64(uint64_t x) { return mix64(x + kGolden); }
+
+// Word at p with `avail` bytes left in the region (zero-padded).
+__device__ __forceinline__ uint64_t load_word(const uint8_t *p, uint64_t avail) {
+    uint64_t v = 0;
+    if (avail >= 8 && ((uintptr_t)p & 7) == 0) return *reinterpret_cast<const uint64_t *>(p);
+    for (uint64_t t = 0; t < 8 && t < avail; ++t) v |= (uint64_t)p[t] << (8 * t);
+    return v;
+}
+
+// This block's share of the digest terms of bytes [off, end) of a region of
+// len bytes at p (off a multiple of 8), reduced over each warp: lane 0 of
+// every warp returns its warp's sum, the other lanes a partial value to
+// ignore.
+__device__ __forceinline__ unsigned long long digest_range(const uint8_t *p, uint64_t len,
+                                                           uint64_t off, uint64_t end) {
+    unsigned long long acc = 0;
+    const uint64_t j0 = off / 8, j1 = (end + 7) / 8;
+    if (((uintptr_t)(p + off) & 15) == 0) {
+        // two words per 16-byte load
+        const uint64_t full = (end - off) / 16;
+        const uint4 *q = reinterpret_cast<const uint4 *>(p + off);
+        for (uint64_t i = threadIdx.x; i < full; i += blockDim.x) {
+            const uint4 v = q[i];
+            const uint64_t w0 = ((uint64_t)v.y << 32) | v.x, w1 = ((uint64_t)v.w << 32) | v.z;
+            const uint64_t j = j0 + 2 * i;
+            acc += mix64(w0 + j * kGolden) + mix64(w1 + (j + 1) * kGolden);
+        }
+        for (uint64_t j = j0 + 2 * full + threadIdx.x; j < j1; j += blockDim.x)
+            acc += mix64(load_word(p + 8 * j, len - 8 * j) + j * kGolden);
+    } else {
+        for (uint64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x)
+            acc += mix64(load_word(p + 8 * j, len - 8 * j) + j * kGolden);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+}  // namespace phos

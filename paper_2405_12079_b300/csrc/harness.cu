@@ -5,20 +5,13 @@
 #include <vector>
 
 #include "../../include/phos_harness.h"
+#include "digest_dev.cuh"
 #include "internal.h"
 
 namespace phos {
 
-constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
 constexpr uint64_t kHTile = 256 * 1024;  // bytes per CTA work item
 constexpr int kMaxEnt = 64;
-
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-__device__ __forceinline__ uint64_t sm64(uint64_t x) { return mix64(x + kGolden); }
 
 struct Ent {
     uint64_t ptr, len;
@@ -41,13 +34,6 @@ __device__ __forceinline__ int find_ent(const EntBatch &b, uint32_t t) {
     return lo;
 }
 
-__device__ __forceinline__ uint64_t load_word(const uint8_t *p, uint64_t avail) {
-    uint64_t v = 0;
-    if (avail >= 8 && ((uintptr_t)p & 7) == 0) return *reinterpret_cast<const uint64_t *>(p);
-    for (uint64_t t = 0; t < 8 && t < avail; ++t) v |= (uint64_t)p[t] << (8 * t);
-    return v;
-}
-
 __global__ void __launch_bounds__(512) k_digest(const __grid_constant__ EntBatch b,
                                                 unsigned long long *out) {
     __shared__ unsigned long long s_acc;
@@ -57,26 +43,8 @@ __global__ void __launch_bounds__(512) k_digest(const __grid_constant__ EntBatch
         const Ent &e = b.e[find_ent(b, t)];
         const uint64_t off = (uint64_t)(t - e.tile0) * kHTile;
         const uint64_t end = min(off + kHTile, e.len);
-        const uint8_t *p = reinterpret_cast<const uint8_t *>(e.ptr);
-        unsigned long long acc = 0;
-        const uint64_t j0 = off / 8, j1 = (end + 7) / 8;
-        if (((uintptr_t)(p + off) & 15) == 0) {
-            // two words per 16-byte load
-            const uint64_t full = (end - off) / 16;
-            const uint4 *q = reinterpret_cast<const uint4 *>(p + off);
-            for (uint64_t i = threadIdx.x; i < full; i += blockDim.x) {
-                uint4 v = q[i];
-                uint64_t w0 = ((uint64_t)v.y << 32) | v.x, w1 = ((uint64_t)v.w << 32) | v.z;
-                uint64_t j = j0 + 2 * i;
-                acc += mix64(w0 + j * kGolden) + mix64(w1 + (j + 1) * kGolden);
-            }
-            for (uint64_t j = j0 + 2 * full + threadIdx.x; j < j1; j += blockDim.x)
-                acc += mix64(load_word(p + 8 * j, e.len - 8 * j) + j * kGolden);
-        } else {
-            for (uint64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x)
-                acc += mix64(load_word(p + 8 * j, e.len - 8 * j) + j * kGolden);
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const unsigned long long acc =
+            digest_range(reinterpret_cast<const uint8_t *>(e.ptr), e.len, off, end);
         if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&s_acc, acc);
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -79,6 +79,17 @@ phos_status validate_impl(const phos_table_t *t, const uint8_t *d_perm, const ui
 
 }  // namespace phos
 
+struct phos_table;
+namespace phos {
+// Digest buffers bufs of live memory on the device and compare each with
+// d_manifest[buf] (PHOS_ECORRUPT in d_status and the lowest bad index in
+// *d_bad on a mismatch).  d_acc (u64[n]) and d_cnt (u32[n]) start zeroed
+// and are left zeroed.  Asynchronous on s.
+phos_status verify_buffers(const phos_table *t, const std::vector<uint32_t> &bufs,
+                           const uint64_t *d_manifest, unsigned long long *d_acc,
+                           uint32_t *d_cnt, uint32_t *d_status, int *d_bad, cudaStream_t s);
+}  // namespace phos
+
 struct phos_table {
     int device = 0;
     uint32_t n = 0;

@@ -56,6 +56,7 @@ _SIGS = {
     "phos_validate_noalloc": (_i32, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _u64,
                                       _vp, _vp]),
     "phos_image_bytes": (_u64, [_vp]),
+    "phos_image_manifest": (_i32, [_vp, _vp, _u64, _vp, _vp]),
     "phos_image_offsets": (_i32, [_vp, _vp]),
     "phos_harness_digest": (_i32, [_vp, _vp, _u32, _vp, _vp]),
     "phos_harness_mutate": (_i32, [_vp, _u64, _u64, _vp, _u32, _vp, _u32, _vp, _u32, _vp]),
@@ -148,13 +149,13 @@ class CkptStats(_c.Structure):
 
 class RestoreDesc(_c.Structure):
     _fields_ = [("access_bytes", _u32), ("flags", _u32), ("chunk", _u64), ("image", _vp),
-                ("image_bytes", _u64), ("d_present", _vp)]
+                ("image_bytes", _u64), ("d_present", _vp), ("d_manifest", _vp)]
 
 
 class RestoreStats(_c.Structure):
     _fields_ = [("kernels", _u64), ("copier_bytes", _u64), ("ondemand_bytes", _u64),
                 ("validated", _u64), ("violations", _u64), ("misspec_round", _c.c_int64),
-                ("done", _u32), ("reserved", _u32)]
+                ("done", _u32), ("corrupt_buf", _i32)]
 
 _lib = None
 
@@ -380,6 +381,12 @@ def harness_drive_ckpt(ckpt, table, seed, quota, kernels, stream=None):
     return int(n.value)
 
 
+def image_manifest(table, image, image_bytes, d_digest, stream=None):
+    """phos_image_manifest: per-buffer digests of a checkpoint image."""
+    return check(lib().phos_image_manifest(table.handle, image, image_bytes, d_digest, stream),
+                 "image_manifest")
+
+
 def harness_fill(ptr, length, key, stream=None):
     return check(lib().phos_harness_fill(ptr, length, key & (2**64 - 1), stream), "harness_fill")
 
@@ -467,10 +474,11 @@ class Restore:
     """One concurrent restore session (phos_restore_*)."""
 
     def __init__(self, table, image, image_bytes, chunk, access_bytes=4, d_present=None,
-                 stream=None, flags=0):
+                 stream=None, flags=0, d_manifest=None):
         """flags: CKPT_NO_SYNC or CKPT_CONCURRENT (the same bits as for
-        checkpoints)."""
-        d = RestoreDesc(access_bytes, flags, chunk, image, image_bytes, d_present)
+        checkpoints); d_manifest: device u64[n] from image_manifest, to
+        verify every restored buffer."""
+        d = RestoreDesc(access_bytes, flags, chunk, image, image_bytes, d_present, d_manifest)
         h = _vp()
         check(lib().phos_restore_begin(table.handle, _c.byref(d), stream, _c.byref(h)),
               "restore_begin")

@@ -11,6 +11,7 @@ movement and validation happen in libphos.so; this module only sequences
 the calls.
 """
 import ctypes
+import time
 
 import numpy as np
 import torch
@@ -104,14 +105,22 @@ class DeviceProcess:
                           max_passes, stop_bytes)
 
     def _ckpt(self, mode, image, quota, chunk, staging, staging_bytes, max_passes=0,
-              stop_bytes=0):
+              stop_bytes=0, mark=None, finish_times=None, logs=True):
+        """One checkpoint session, round by round.  mark(phase) is called as
+        each phase of a round is enqueued (copier, cow / dirty_marking,
+        app_kernel, validate, finish, end); finish_times receives the host
+        time finish took after the device had drained; logs=False returns
+        the statistics only."""
         s = self.stream()
         c = phos.Checkpoint(self.table, mode, image.data_ptr(), image.numel(), chunk, 4,
                             staging.data_ptr() if staging is not None else None, staging_bytes, s)
+        mark = mark or (lambda name: None)
+        pre = "cow" if mode & phos.CKPT_COW else "dirty_marking"
         k, misspec = 0, False
         K = len(self.kernels)
         prev, passes = None, 0
         while k < K:
+            mark("copier")
             if c.advance(quota):
                 db = self.dirty_bytes(c) if max_passes else 0
                 if passes < max_passes and db > stop_bytes and (prev is None or db < prev):
@@ -120,13 +129,27 @@ class DeviceProcess:
                 else:
                     break
             pk = self.kernels[k]
+            mark(pre)
             c.before_kernel(pk.speculate(self.table, self.perm))
+            mark("app_kernel")
             self.run_kernel(k)
+            mark("validate")
             misspec = c.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1
             if misspec:
                 break
+        mark("finish")
+        if finish_times is not None:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
         c.finish()
+        if finish_times is not None:
+            finish_times.append(time.perf_counter() - t0)
+        mark("end")
+        if not logs:
+            st = c.stats()
+            c.close()
+            return st
         out = dict(stats=c.stats(), cow=c.log(0), copier=c.log(1), dirty=c.log(2)[:, 0],
                    passes=c.log(3), kernels_run=k)
         c.close()
@@ -152,12 +175,15 @@ class DeviceProcess:
         d = c.log(2)[:, 0].astype(np.int64)
         return int(self.layout.size[d].sum()) if len(d) else 0
 
-    def run_restore(self, image, quota, chunk, d_present=None, rounds="sync"):
-        """Concurrent restore followed by the rest of the kernels."""
+    def run_restore(self, image, quota, chunk, d_present=None, rounds="sync", d_manifest=None):
+        """Concurrent restore followed by the rest of the kernels;
+        d_manifest: verify every restored buffer against it (finish raises
+        PHOS_ECORRUPT on a mismatch)."""
         s = self.stream()
         r = phos.Restore(self.table, image.data_ptr(), image.numel(), chunk, 4,
                          d_present.data_ptr() if d_present is not None else None, s,
-                         self._flags(rounds))
+                         self._flags(rounds),
+                         d_manifest.data_ptr() if d_manifest is not None else None)
         k = 0
         K = len(self.kernels)
         while k < K:

@@ -271,8 +271,15 @@ def test_cancelled_requests_leave_the_others_exact():
         assert x["state"] == (4 if q in cancel else 2) and x["status"] == 0
     assert st["cancelled"] == 3
     exp_dev, exp_host = w.expected(skip=cancel)
-    assert np.array_equal(w.dev.cpu().numpy(), exp_dev)
-    assert np.array_equal(w.host.numpy(), exp_host)
+    dev, host = w.dev.cpu().numpy(), w.host.numpy()
+    diff = [q for q, r in enumerate(w.reqs)
+            if not np.array_equal(dev[r["dev_off"]:r["dev_off"] + r["lay"].arena_bytes],
+                                  exp_dev[r["dev_off"]:r["dev_off"] + r["lay"].arena_bytes]) or
+            not np.array_equal(host[r["host_off"]:r["host_off"] + r["img"]],
+                               exp_host[r["host_off"]:r["host_off"] + r["img"]])]
+    assert diff == [], (diff, states)
+    assert np.array_equal(dev, exp_dev)
+    assert np.array_equal(host, exp_host)
     with pytest.raises(phos.PhosError):
         srv2 = phos.Server(1, staging.data_ptr(), staging.numel())
         try:
