@@ -21,7 +21,7 @@ def run(*args):
 
 
 def test_training_line_contract():
-    line = run("--scale", "0.01", "--steps", "2", "--warmup", "3")
+    line = run("--scale", "0.01", "--steps", "2", "--warmup", "3", "--serving-window", "2")
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
               "roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks"):
@@ -35,6 +35,16 @@ def test_training_line_contract():
         assert k in r
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert "all_cores" in line["cpu_baseline"]["loops"]
+    # the batched, serving and restore forms, measured in the same run
+    arms = line["arms"]
+    assert set(arms) == {"batched", "serving", "restore"}
+    for name, arm in arms.items():
+        assert "error" not in arm, (name, arm)
+        assert arm["value"] > 0 and arm["gpu_launches"] > 0 and "clocks" in arm
+    assert arms["batched"]["status"] == 0 and "roofline" in arms["batched"]
+    assert arms["serving"]["p99_ms"] > 0 and "one_at_a_time" in arms["serving"]
+    assert arms["restore"]["verified"]["final_memory_equals_stw_restore_plus_replay"]
 
 
 def test_reference_arm_contract():
