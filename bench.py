@@ -194,7 +194,8 @@ def across_ranks(ms, moved, recs, world):
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+         "clocks.mem,clocks.max.mem")
 
     def __init__(self, index):
         self.index = index
@@ -203,7 +204,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
@@ -213,7 +214,7 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
         out, _ = self.p.communicate(timeout=10)
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, mem, mem_mx = [], None, set(), [], None
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
                  "sw_power_cap"]
         for line in out.strip().splitlines():
@@ -228,8 +229,16 @@ class Clocks:
             for nm, v in zip(names[1:], f[5:9]):
                 if v.lower() in ("active", "yes", "1"):
                     reasons.add(nm)
+            if len(f) >= 11:
+                try:
+                    mem.append(float(f[9]))
+                    mem_mx = float(f[10])
+                except ValueError:
+                    pass
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "mem_mhz": float(np.median(mem)) if mem else None, "mem_max_mhz": mem_mx,
+                "mem_mhz_min": float(np.min(mem)) if mem else None}
 
 
 class Marks:
@@ -433,16 +442,25 @@ def run_gpu(args, rank, world):
             best = min(best, x0.elapsed_time(x1))
         return best
 
-    # the step is bound by PCIe, and HBM-bound kernels timed right after it
-    # ran slow until the GPU's clocks came back up (measured: 430-480 G
-    # records/s cold against 620-630 warm); keep the GPU busy for ~1.5 s
-    # first
+    # one launch over all 200 distinct traces (260M records, 2.1 GB, 16x L2)
+    all_tr = torch.cat([p.d_trace for p in dp.kernels])
+    all_n = all_tr.numel() // 8
+    aperm = torch.stack(perms).max(dim=0).values.contiguous()
+
+    def val_all():
+        phos.validate(dp.table, aperm.data_ptr(), all_tr.data_ptr(), all_n, 4, bm.data_ptr(),
+                      cnt.data_ptr(), vv.data_ptr(), vv.data_ptr() + 4 * nvw, None, 0,
+                      stw.data_ptr(), s)
+    # the step is bound by PCIe; HBM-bound kernels timed right after it ran
+    # slow (430-480 G records/s against 620-630 after sustained load, in a
+    # probe that alternated both): ~1.5 s of back-to-back launches first,
+    # with the clocks (SM and memory) sampled over this whole block
+    rclk = Clocks(dev)
+    rclk.start()
     t_warm = time.time() + 1.5
     while time.time() < t_warm:
-        for p, pm in zip(dp.kernels[:50], perms[:50]):
-            phos.validate(dp.table, pm.data_ptr(), p.d_trace.data_ptr(), p.n_rec, 4,
-                          bm.data_ptr(), cnt.data_ptr(), vv.data_ptr(), vv.data_ptr() + 4 * nvw,
-                          None, 0, stw.data_ptr(), s)
+        for _ in range(20):
+            val_all()
         torch.cuda.synchronize()
     val_ms = ev_ms(lambda: [phos.validate(dp.table, pm.data_ptr(), p.d_trace.data_ptr(), p.n_rec,
                                           4, bm.data_ptr(), cnt.data_ptr(), vv.data_ptr(),
@@ -461,18 +479,12 @@ def run_gpu(args, rank, world):
                                          vv.data_ptr() + 4 * nvw, None, 0, stw.data_ptr(), s))
     cat_gbs = cat_n * 8.125 / (cat_ms * 1e6)
     del cat
-    # one launch over all 200 distinct traces (260M records, 2.1 GB, 16x L2),
-    # L2 flushed before each repetition
+    # the 260M-record launch, L2 flushed (a 256 MB write) before each repetition
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    all_tr = torch.cat([p.d_trace for p in dp.kernels])
-    all_n = all_tr.numel() // 8
-    aperm = torch.stack(perms).max(dim=0).values.contiguous()
     all_ms = 1e30
-    for _ in range(3):
+    for _ in range(5):
         flush.zero_()
-        all_ms = min(all_ms, ev_ms(lambda: phos.validate(
-            dp.table, aperm.data_ptr(), all_tr.data_ptr(), all_n, 4, bm.data_ptr(), cnt.data_ptr(),
-            vv.data_ptr(), vv.data_ptr() + 4 * nvw, None, 0, stw.data_ptr(), s), reps=1))
+        all_ms = min(all_ms, ev_ms(val_all, reps=1))
     all_gbs = all_n * 8.125 / (all_ms * 1e6)
     del all_tr, flush
     # CoW copy kernel alone: the step's largest buffers live -> staging
@@ -488,6 +500,7 @@ def run_gpu(args, rank, world):
     d2d_ms = ev_ms(lambda: phos.cow_copy(dp.table, cdesc.data_ptr(), len(rows),
                                          staging.data_ptr(), staging_bytes, stw.data_ptr(), s))
     d2d_gbs = 2 * off / (d2d_ms * 1e6)
+    roof_clocks = rclk.stop()
 
     # end to end: the step's traces come from pinned host memory each step
     # (host->device inside the timed region) and its stats are read back
@@ -570,6 +583,7 @@ def run_gpu(args, rank, world):
                  "frac": d2d_gbs / hbm, "traffic": 2 * off * 0.99,
                  "traffic_source": "profiles/copy_main_d2d_2GB.md (DRAM bytes = 0.99 x "
                                    "algorithmic), scaled to this launch"}],
+            "rooflines_clocks": roof_clocks,
             "breakdown_ms_per_step": {k: v / args.steps for k, v in phase.items()},
             "cow": {"cow_bytes": a_last["cow_bytes"], "direct_bytes": a_last["direct_bytes"],
                     "kernels": a_last["kernels"], "misspec_round": a_last["misspec_round"]},
@@ -1060,7 +1074,9 @@ def run_default(args, rank, world):
                          ("serving", lambda a: serving_line(a, world, window=args.serving_window)),
                          ("restore", lambda a: restore_line(a, world))):
             a = copy.copy(args)
-            a.steps, a.warmup = 5, 3
+            # the batched arm's launches take ~5 ms: 200 of them give the
+            # clocks sampler about a second
+            a.steps, a.warmup = (200, 10) if name == "batched" else (5, 3)
             try:
                 arms[name] = fn(a)
             except Exception as e:              # an arm that fails is reported, not fatal
@@ -1303,9 +1319,14 @@ def run_rounds(args, rank, world):
     staging = torch.empty(a256(dp.image_bytes / 20), dtype=torch.uint8, device="cuda")
     quota = a256(dp.image_bytes / 2000)
 
+    d_perms = dp.device_perms()          # device speculation of every kernel, one launch
+    nn = max(lay.n, 1)
+
     def session(rounds, cow=False):
-        mode = (phos.CKPT_COW if cow else phos.CKPT_RECOPY) | {
-            "sync": 0, "nosync": phos.CKPT_NO_SYNC, "concurrent": phos.CKPT_CONCURRENT}[rounds]
+        """rounds: sync / nosync / concurrent, or device (CoW only: every
+        round's decisions on the device, perms from device speculation)."""
+        device = rounds == "device"
+        mode = (phos.CKPT_COW if cow else phos.CKPT_RECOPY) | runner.DeviceProcess._flags(rounds)
         c = phos.Checkpoint(dp.table, mode, image.data_ptr(), image.numel(), 4 << 20, 4,
                             staging.data_ptr() if cow else None, staging.numel() if cow else 0, s)
         torch.cuda.synchronize()
@@ -1315,7 +1336,10 @@ def run_rounds(args, rank, world):
             if c.advance(quota):
                 break
             pk = dp.kernels[k]
-            c.before_kernel(pk.speculate(dp.table, dp.perm))
+            if device:
+                c.before_kernel_dev(d_perms.data_ptr() + k * nn)
+            else:
+                c.before_kernel(pk.speculate(dp.table, dp.perm))
             dp.run_kernel(k)
             c.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1
@@ -1356,11 +1380,13 @@ def run_rounds(args, rank, world):
 
     for r in ("sync", "nosync", "concurrent"):
         session(r)
+    session("device", cow=True)
     l0 = phos.launch_count()
     res = {"kernels_alone": alone()}
     for r in ("sync", "nosync", "concurrent"):
         res["recopy_" + r] = session(r)
         res["cow_" + r] = session(r, cow=True)
+    res["cow_device"] = session("device", cow=True)
     for r in ("sync", "concurrent"):
         native(r)
         res["native_recopy_" + r] = native(r)

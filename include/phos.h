@@ -484,6 +484,23 @@ enum { PHOS_CKPT_NO_SYNC = 0x100 };
  * anyway).  Every host decision, and so every result, is the lockstep
  * mode's. */
 enum { PHOS_CKPT_CONCURRENT = 0x200 };
+/* OR'ed into mode (CoW sessions) or restore flags (implies
+ * PHOS_CKPT_NO_SYNC; not with PHOS_CKPT_CONCURRENT or a manifest): every
+ * per-round decision is taken on the device from device-resident state --
+ * the copier's pieces, the CoW set with its first-fit staging allocation
+ * (or the direct copy when staging is full), the restore need set, and the
+ * flags the validation rule reads -- so a round is a fixed sequence of
+ * launches on the caller's stream and needs no host data: pass the round's
+ * speculated permissions as a device array to *_before_kernel_dev (for
+ * example rows of phos_speculate_device's output).  Every decision follows
+ * the same rules as the host's, so lists and images are the lockstep
+ * mode's.  The host does not learn when the copier finishes: advance
+ * reports done only after a mis-speculation (restore: after its
+ * roll-back), rounds after the end are no-ops for the protocol, and finish
+ * drains the rest, then reads the device's logs (capacity fixed at begin;
+ * PHOS_ENOMEM if exceeded).  Copies are all SM-issued (no DMA host legs:
+ * the host does not see the pieces). */
+enum { PHOS_CKPT_DEVICE = 0x400 };
 
 typedef struct {
     uint32_t mode;           /* PHOS_CKPT_COW (Sec. 4.2) or PHOS_CKPT_RECOPY
@@ -533,6 +550,9 @@ phos_status phos_ckpt_before_kernel(phos_ckpt_t *c, const uint8_t *perm);
  * store victims that were in flight or done join the dirty set. */
 phos_status phos_ckpt_after_kernel(phos_ckpt_t *c, const uint64_t *d_trace, uint64_t n_rec,
                                    int *misspec);
+/* PHOS_CKPT_DEVICE sessions: the round's CoW set from d_perm (device
+ * u8[n], read when the round runs on the stream), decided on the device. */
+phos_status phos_ckpt_before_kernel_dev(phos_ckpt_t *c, const uint8_t *d_perm);
 /* Drain the rest; recopy: quiesce point t2, recopy the dirty set whole.
  * Synchronises. */
 phos_status phos_ckpt_finish(phos_ckpt_t *c);
@@ -619,6 +639,9 @@ phos_status phos_restore_advance(phos_restore_t *r, uint64_t quota, int *done);
 /* Copy the not-yet-restored bytes of every buffer with perm != 0 before
  * the kernel runs (the kernel waits for them). */
 phos_status phos_restore_before_kernel(phos_restore_t *r, const uint8_t *perm);
+/* PHOS_CKPT_DEVICE sessions: the round's need set from d_perm (device
+ * u8[n]), decided on the device. */
+phos_status phos_restore_before_kernel_dev(phos_restore_t *r, const uint8_t *d_perm);
 /* Validate; an access (load or store) to a buffer that was not present
  * before the kernel restores every buffer stop-the-world from the image
  * and sets *misspec = 1: the caller replays its kernels from the first

@@ -40,7 +40,8 @@ struct CopyRes {
 
 struct CopyArgs {
     const phos_copy_t *list;
-    uint32_t n;
+    uint32_t n;            // descriptors (the capacity when n_dev is set)
+    const uint32_t *n_dev; // optional: the count, read on the device (<= n)
     TableDev tab;
     uint8_t *staging;
     uint64_t staging_bytes;
@@ -56,19 +57,24 @@ struct CopyArgs {
     uint32_t *done;        // [n]
 };
 
+__device__ __forceinline__ uint32_t copy_count(const CopyArgs &a) {
+    return a.n_dev ? min(*a.n_dev, a.n) : a.n;
+}
+
 __global__ void __launch_bounds__(1024) k_copy_prep(const CopyArgs a) {
     __shared__ unsigned long long s_warp[32];
     __shared__ unsigned long long s_carry;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t N = copy_count(a);
     if (tid == 0) {
         s_carry = 0;
         a.prefix[0] = 0;
     }
     __syncthreads();
-    for (uint32_t b0 = 0; b0 < a.n; b0 += blockDim.x) {
+    for (uint32_t b0 = 0; b0 < N; b0 += blockDim.x) {
         const uint32_t d = b0 + tid;
         unsigned long long nt = 0;
-        if (d < a.n) {
+        if (d < N) {
             const phos_copy_t c = a.list[d];
             const uint32_t dir = c.flags & PHOS_COPY_DIR_MASK;
             bool ok = (c.flags & ~(uint32_t)(PHOS_COPY_DIR_MASK | PHOS_COPY_MARK_PRESENT)) == 0 &&
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(1024) k_copy_prep(const CopyArgs a) {
             total += s_warp[q];
         }
         const unsigned long long carry = s_carry;
-        if (d < a.n) a.prefix[d + 1] = carry + woff + incl;
+        if (d < N) a.prefix[d + 1] = carry + woff + incl;
         __syncthreads();
         if (tid == 0) s_carry = carry + total;
         __syncthreads();
@@ -157,11 +163,12 @@ __global__ void __launch_bounds__(1024) k_copy_prep(const CopyArgs a) {
 __global__ void __launch_bounds__(512, 3) k_copy_main(const CopyArgs a) {
     __shared__ uint32_t s_d;
     __shared__ uint32_t s_last;
-    const uint64_t total = a.prefix[a.n];
+    const uint32_t N = copy_count(a);
+    const uint64_t total = a.prefix[N];
     for (uint64_t t = blockIdx.x; t < total; t += gridDim.x) {
         if (threadIdx.x == 0) {
             // last descriptor whose prefix <= t
-            uint32_t lo = 0, cnt = a.n + 1;
+            uint32_t lo = 0, cnt = N + 1;
             while (cnt > 0) {
                 uint32_t half = cnt >> 1;
                 if (a.prefix[lo + half] <= t) {
@@ -200,7 +207,8 @@ static uint32_t g_ctas_per_sm = 3;
 static phos_status launch_copy(const phos_table_t *t, const phos_copy_t *d_list, uint32_t n,
                                void *staging, uint64_t staging_bytes, const void *image,
                                uint64_t image_bytes, uint32_t *d_present, uint32_t *d_status,
-                               uint32_t allow, phos_stream_t stream, const char *who) {
+                               uint32_t allow, phos_stream_t stream, const char *who,
+                               const uint32_t *d_n = nullptr) {
     if (!t) return fail(PHOS_EINVAL, "%s: table is NULL", who);
     if (n == 0) return PHOS_OK;
     if (!d_list) return fail(PHOS_EINVAL, "%s: d_list is NULL", who);
@@ -222,6 +230,7 @@ static phos_status launch_copy(const phos_table_t *t, const phos_copy_t *d_list,
     CopyArgs a;
     a.list = d_list;
     a.n = n;
+    a.n_dev = d_n;
     a.tab = t->view;
     a.staging = static_cast<uint8_t *>(stg);
     a.staging_bytes = stg ? staging_bytes : 0;
@@ -243,6 +252,15 @@ static phos_status launch_copy(const phos_table_t *t, const phos_copy_t *d_list,
     count_launch();
     PHOS_CUDA(cudaGetLastError());
     return PHOS_OK;
+}
+
+phos_status copy_device_count(const phos_table_t *t, const phos_copy_t *d_list, uint32_t cap,
+                              const uint32_t *d_n, void *staging, uint64_t staging_bytes,
+                              const void *image, uint64_t image_bytes, uint32_t *d_present,
+                              uint32_t *d_status, phos_stream_t stream) {
+    if (!d_n) return fail(PHOS_EINVAL, "copy_device_count: NULL count");
+    return launch_copy(t, d_list, cap, staging, staging_bytes, image, image_bytes, d_present,
+                       d_status, 0x1Eu, stream, "copy_device_count", d_n);
 }
 
 }  // namespace phos

@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include <algorithm>
+#include <deque>
 #include <vector>
 
 #include "internal.h"
@@ -144,6 +145,8 @@ struct Session {
     // arena (recycled at synchronisations), validation outputs and rule
     // state in device memory, the mis-speculation word mapped
     bool nosync = false;
+    // device-decided rounds: the round's perm and rule flags on the device
+    const uint8_t *perm_dev = nullptr, *flags_dev = nullptr;
     uint8_t *h_up = nullptr, *d_up = nullptr;
     size_t up_cap = 0, up_used = 0, slot = 0;
     uint64_t *d_acc = nullptr;      // u64[8], see k_rule
@@ -151,12 +154,16 @@ struct Session {
     uint8_t *d_dirty = nullptr;     // u8[n]
     int64_t *h_flag = nullptr, *d_flag = nullptr;
     // concurrent sessions: the copier's own stream, a clone of the table
-    // (its own copy-engine scratch), one event per copier batch (ring)
-    static constexpr uint32_t kRing = 1024;
+    // (its own copy-engine scratch), one event per copier batch, kept until
+    // that batch has completed (batches complete in order on the copier
+    // stream; an event is reused only once its batch is known complete, so
+    // a wait never lands on a later batch than the one it names)
     cudaStream_t cs = nullptr;
     phos_table_t *tc = nullptr;
     cudaEvent_t app_ev = nullptr;
-    cudaEvent_t bev[kRing] = {};
+    std::deque<std::pair<uint64_t, cudaEvent_t>> bq;   // in flight, ascending
+    std::vector<cudaEvent_t> ev_free;
+    uint64_t batch_done = 0;            // every batch <= this has completed
     uint64_t batch = 0;                 // copier batches issued on cs
     std::vector<uint64_t> last_batch;   // per buffer: batch of its last piece
 
@@ -205,7 +212,6 @@ struct Session {
         r = phos_table_create(b.data(), n, &tc);
         if (r) return r;
         PHOS_CUDA(cudaEventCreateWithFlags(&app_ev, cudaEventDisableTiming));
-        for (cudaEvent_t &e : bev) PHOS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         last_batch.assign(n, 0);
         return PHOS_OK;
     }
@@ -217,10 +223,39 @@ struct Session {
         return e;
     }
 
-    // Make the caller's stream wait for copier batch b (an event of the
-    // ring; a newer batch in the same slot only waits longer).
+    // Record the event of copier batch b (b = the previous batch + 1) on
+    // the copier stream, retiring the events of completed batches first.
+    phos_status record_batch(uint64_t b) {
+        while (!bq.empty()) {
+            const cudaError_t q = cudaEventQuery(bq.front().second);
+            if (q == cudaErrorNotReady) {
+                cudaGetLastError();
+                break;
+            }
+            if (q != cudaSuccess) return cuda_fail(q, "copier batch event");
+            batch_done = bq.front().first;
+            ev_free.push_back(bq.front().second);
+            bq.pop_front();
+        }
+        cudaEvent_t e;
+        if (ev_free.empty()) {
+            PHOS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        } else {
+            e = ev_free.back();
+            ev_free.pop_back();
+        }
+        PHOS_CUDA(cudaEventRecord(e, cs));
+        bq.push_back({b, e});
+        batch = b;
+        return PHOS_OK;
+    }
+
+    // Make the caller's stream wait for copier batch b (and so for every
+    // earlier one).
     phos_status app_wait(uint64_t b) {
-        if (b) PHOS_CUDA(cudaStreamWaitEvent(s, bev[b % kRing], 0));
+        if (!b || b <= batch_done || bq.empty() || b < bq.front().first) return PHOS_OK;
+        const uint64_t k = std::min<uint64_t>(b - bq.front().first, bq.size() - 1);
+        PHOS_CUDA(cudaStreamWaitEvent(s, bq[k].second, 0));
         return PHOS_OK;
     }
 
@@ -255,8 +290,8 @@ struct Session {
         }
         if (tc) phos_table_destroy(tc);
         if (app_ev) cudaEventDestroy(app_ev);
-        for (cudaEvent_t e : bev)
-            if (e) cudaEventDestroy(e);
+        for (auto &be : bq) cudaEventDestroy(be.second);
+        for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
         if (h_up) cudaFreeHost(h_up);
         if (d_up) cudaFree(d_up);
         if (d_acc) cudaFree(d_acc);
@@ -414,19 +449,21 @@ struct Session {
         const uint32_t nvw = std::max((n + 31) / 32, 1u);
         // the validation kernel's last CTA applies the rule when it can;
         // otherwise (ring variant, empty trace) k_rule does
+        const uint8_t *pp = perm_dev ? perm_dev : d_up + slot;
+        const uint8_t *ff = flags_dev ? flags_dev : d_up + slot + n;
         ProtoRule pr;
-        pr.flags = d_up + slot + n;
+        pr.flags = ff;
         pr.dirty = d_dirty;
         pr.acc = d_acc;
         pr.h_flag = d_flag;
         pr.round = (int64_t)round - 1;
         pr.kind = rule == 0 ? 1u : (rule == 1 ? 2u : 3u);
         bool fused = false;
-        phos_status r = validate_impl(t, d_up + slot, d_trace, n_rec, w, d_bitmap, d_acc, d_vic,
+        phos_status r = validate_impl(t, pp, d_trace, n_rec, w, d_bitmap, d_acc, d_vic,
                                       d_vic + nvw, nullptr, 0, d_status, s, &pr, &fused);
         if (r) return r;
         if (!fused) {
-            k_rule<<<1, 256, 0, s>>>(rule == 2 ? d_vic : d_vic + nvw, d_up + slot + n, n,
+            k_rule<<<1, 256, 0, s>>>(rule == 2 ? d_vic : d_vic + nvw, ff, n,
                                      rule ? 1 : 0, (int64_t)round - 1, d_dirty, d_acc, d_flag);
             PHOS_CUDA(cudaGetLastError());
             count_launch();
@@ -553,15 +590,25 @@ struct phos_ckpt {
     // concurrent: copier batch of the last staging release, and the latest
     // release batch the caller's stream has waited for
     uint64_t release_batch = 0, waited_release = 0;
+    DevRounds *dr = nullptr;      // PHOS_CKPT_DEVICE: decisions on the device
+    ~phos_ckpt() {
+        ss.sync_streams();
+        delete dr;
+    }
 };
 
 extern "C" phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_desc_t *d,
                                        phos_stream_t stream, phos_ckpt_t **out) {
     if (!t || !d || !out) return fail(PHOS_EINVAL, "ckpt_begin: NULL argument");
     *out = nullptr;
-    const uint32_t mode = d->mode & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT);
+    const uint32_t mode =
+        d->mode & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT | PHOS_CKPT_DEVICE);
     if (mode != PHOS_CKPT_COW && mode != PHOS_CKPT_RECOPY)
         return fail(PHOS_EINVAL, "ckpt_begin: mode %u", d->mode);
+    if ((d->mode & PHOS_CKPT_DEVICE) &&
+        (mode != PHOS_CKPT_COW || (d->mode & PHOS_CKPT_CONCURRENT)))
+        return fail(PHOS_EINVAL, "ckpt_begin: PHOS_CKPT_DEVICE is for CoW sessions, without "
+                                 "PHOS_CKPT_CONCURRENT");
     if (d->access_bytes == 0 || d->chunk == 0 || d->chunk % 256)
         return fail(PHOS_EINVAL, "ckpt_begin: access_bytes >= 1, chunk a multiple of 256");
     if (!d->image || d->image_bytes < t->image_bytes)
@@ -577,9 +624,18 @@ extern "C" phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_de
         delete c;
         return r;
     }
-    if ((d->mode & PHOS_CKPT_NO_SYNC) && !c->ss.nosync && (r = c->ss.init_nosync())) {
+    if ((d->mode & (PHOS_CKPT_NO_SYNC | PHOS_CKPT_DEVICE)) && !c->ss.nosync &&
+        (r = c->ss.init_nosync())) {
         delete c;
         return r;
+    }
+    if (d->mode & PHOS_CKPT_DEVICE) {
+        c->dr = new DevRounds();
+        if ((r = c->dr->init(t, 2, d->chunk, d->d_staging ? d->staging_bytes : 0, false,
+                             c->ss.s))) {
+            delete c;
+            return r;
+        }
     }
     c->mode = mode;
     c->staging = mode == PHOS_CKPT_COW ? d->d_staging : nullptr;
@@ -640,10 +696,7 @@ static phos_status ckpt_advance(phos_ckpt *c, uint64_t quota) {
     phos_status r = S.submit(v, c->staging, c->staging_bytes, c->image, c->image_bytes, nullptr,
                              true);
     if (r) return r;
-    if (S.cs && !v.empty()) {
-        S.batch = b;
-        PHOS_CUDA(cudaEventRecord(S.bev[b % Session::kRing], S.cs));
-    }
+    if (S.cs && !v.empty() && (r = S.record_batch(b))) return r;
     return PHOS_OK;
 }
 
@@ -651,6 +704,19 @@ extern "C" phos_status phos_ckpt_advance(phos_ckpt_t *c, uint64_t quota, int *do
     if (!c) return fail(PHOS_EINVAL, "ckpt_advance: NULL session");
     if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_advance: inside a kernel round");
     phos_status r = PHOS_OK;
+    if (c->dr) {
+        // the device decides; the host only learns of a mis-speculation
+        Session &S = c->ss;
+        if (!c->complete && S.flag() >= 0) {
+            c->misspec = S.flag();
+            c->complete = true;
+        }
+        if (!c->complete)
+            r = c->dr->copier(quota, S.round, c->staging, c->staging_bytes, c->image,
+                              c->image_bytes, nullptr, S.d_status, S.s);
+        if (done) *done = c->complete ? 1 : 0;
+        return r;
+    }
     if (c->ss.nosync && c->mode == PHOS_CKPT_COW && !c->complete && c->ss.flag() >= 0) {
         c->misspec = c->ss.flag();        // the device saw it; finish falls back
         c->complete = true;
@@ -730,6 +796,22 @@ extern "C" phos_status phos_ckpt_before_kernel(phos_ckpt_t *c, const uint8_t *pe
     return PHOS_OK;
 }
 
+extern "C" phos_status phos_ckpt_before_kernel_dev(phos_ckpt_t *c, const uint8_t *d_perm) {
+    if (!c) return fail(PHOS_EINVAL, "ckpt_before_kernel_dev: NULL session");
+    if (!c->dr) return fail(PHOS_EINVAL, "ckpt_before_kernel_dev: not a PHOS_CKPT_DEVICE session");
+    if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_before_kernel_dev: after_kernel missing");
+    if (c->complete) return fail(PHOS_EINVAL, "ckpt_before_kernel_dev: checkpoint already complete");
+    if (!d_perm && c->ss.n) return fail(PHOS_EINVAL, "ckpt_before_kernel_dev: d_perm is NULL");
+    Session &S = c->ss;
+    phos_status r = c->dr->action(d_perm, S.round, c->staging, c->staging_bytes, c->image,
+                                  c->image_bytes, nullptr, S.d_status, S.s);
+    if (r) return r;
+    S.perm_dev = d_perm;
+    S.flags_dev = c->dr->flags();
+    c->in_kernel = true;
+    return PHOS_OK;
+}
+
 static phos_status stw_checkpoint(phos_ckpt *c) {
     Session &S = c->ss;
     std::vector<phos_copy_t> v;
@@ -795,6 +877,28 @@ extern "C" phos_status phos_ckpt_finish(phos_ckpt_t *c) {
     if (c->in_kernel) return fail(PHOS_EINVAL, "ckpt_finish: inside a kernel round");
     Session &S = c->ss;
     phos_status r;
+    if (c->dr && !c->finished) {
+        if ((r = S.collect(nullptr))) return r;
+        if (S.flag() >= 0) {
+            c->misspec = S.flag();
+            if ((r = stw_checkpoint(c))) return r;
+        } else {
+            // drain what the copier has not moved yet
+            r = c->dr->copier(~0ull >> 2, S.round, c->staging, c->staging_bytes, c->image,
+                              c->image_bytes, nullptr, S.d_status, S.s);
+            if (r) return r;
+        }
+        if ((r = S.sync())) return r;
+        uint64_t ctr[6];
+        std::vector<uint8_t> st;
+        if ((r = c->dr->collect(S.copier_log, c->cow_log, ctr, &st))) return r;
+        c->copier_bytes = ctr[2];
+        c->cow_bytes = ctr[3];
+        c->direct_bytes = ctr[4];
+        c->complete = true;
+        c->finished = true;
+        return PHOS_OK;
+    }
     if (S.nosync && !c->finished) {
         // everything enqueued has run: the rule's outcome is final
         r = S.collect(c->mode == PHOS_CKPT_RECOPY ? &c->dirty : nullptr);
@@ -944,8 +1048,11 @@ struct phos_restore {
         return verify_buffers(ss.t, bufs, d_manifest, d_vacc, d_vcnt, ss.d_status, d_bad, st);
     }
 
+    DevRounds *dr = nullptr;      // PHOS_CKPT_DEVICE: decisions on the device
+
     ~phos_restore() {
         ss.sync_streams();
+        delete dr;
         if (d_vacc) cudaFree(d_vacc);
         if (d_vcnt) cudaFree(d_vcnt);
         if (h_bad) cudaFreeHost(h_bad);
@@ -970,12 +1077,20 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
     if (!d->image || d->image_bytes < t->image_bytes)
         return fail(PHOS_EINVAL, "restore_begin: image smaller than %llu bytes",
                     (unsigned long long)t->image_bytes);
-    if (d->flags & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT))
+    if (d->flags & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT | PHOS_CKPT_DEVICE))
         return fail(PHOS_EINVAL, "restore_begin: flags %#x", d->flags);
+    if ((d->flags & PHOS_CKPT_DEVICE) && ((d->flags & PHOS_CKPT_CONCURRENT) || d->d_manifest))
+        return fail(PHOS_EINVAL, "restore_begin: PHOS_CKPT_DEVICE goes without "
+                                 "PHOS_CKPT_CONCURRENT and without a manifest");
     phos_restore *r = new phos_restore();
     phos_status e = r->ss.init(t, static_cast<cudaStream_t>(stream), d->access_bytes, d->chunk);
     if (!e && (d->flags & PHOS_CKPT_CONCURRENT)) e = r->ss.init_concurrent();
-    if (!e && (d->flags & PHOS_CKPT_NO_SYNC) && !r->ss.nosync) e = r->ss.init_nosync();
+    if (!e && (d->flags & (PHOS_CKPT_NO_SYNC | PHOS_CKPT_DEVICE)) && !r->ss.nosync)
+        e = r->ss.init_nosync();
+    if (!e && (d->flags & PHOS_CKPT_DEVICE)) {
+        r->dr = new DevRounds();
+        e = r->dr->init(t, 1, d->chunk, 0, d->d_present != nullptr, r->ss.s);
+    }
     if (e) {
         delete r;
         return e;
@@ -1038,8 +1153,7 @@ static phos_status restore_advance(phos_restore *R, uint64_t quota) {
         if ((r = R->verify(landed, S.cs ? S.cs : S.s))) return r;
         if (S.cs) {
             for (uint32_t i : touched) S.last_batch[i] = b;
-            S.batch = b;
-            PHOS_CUDA(cudaEventRecord(S.bev[b % Session::kRing], S.cs));
+            if ((r = S.record_batch(b))) return r;
             ++b;
         }
         v.clear();
@@ -1100,6 +1214,7 @@ static phos_status restore_rollback(phos_restore *R, int64_t k) {
     }
     phos_status r2 = S.submit(v, nullptr, 0, R->image, R->image_bytes, R->d_present);
     if (r2) return r2;
+    if (R->dr && (r2 = R->dr->mark_all(S.s))) return r2;
     return R->verify(all, S.s);
 }
 
@@ -1110,6 +1225,14 @@ extern "C" phos_status phos_restore_advance(phos_restore_t *R, uint64_t quota, i
     if (R->ss.nosync && R->misspec < 0 && R->ss.flag() >= 0) {
         r = restore_rollback(R, R->ss.flag());  // the device saw it
         if (r) return r;
+    }
+    if (R->dr) {
+        Session &S = R->ss;
+        if (R->misspec < 0)
+            r = R->dr->copier(quota, S.round, nullptr, 0, R->image, R->image_bytes, R->d_present,
+                              S.d_status, S.s);
+        if (done) *done = R->misspec >= 0 ? 1 : 0;
+        return r;
     }
     if (!R->all_present()) r = restore_advance(R, quota);
     if (done) *done = R->all_present() ? 1 : 0;
@@ -1165,6 +1288,23 @@ extern "C" phos_status phos_restore_before_kernel(phos_restore_t *R, const uint8
     return PHOS_OK;
 }
 
+extern "C" phos_status phos_restore_before_kernel_dev(phos_restore_t *R, const uint8_t *d_perm) {
+    if (!R) return fail(PHOS_EINVAL, "restore_before_kernel_dev: NULL session");
+    if (!R->dr) return fail(PHOS_EINVAL, "restore_before_kernel_dev: not a PHOS_CKPT_DEVICE session");
+    if (R->in_kernel) return fail(PHOS_EINVAL, "restore_before_kernel_dev: after_kernel missing");
+    if (!d_perm && R->ss.n) return fail(PHOS_EINVAL, "restore_before_kernel_dev: d_perm is NULL");
+    Session &S = R->ss;
+    if (R->misspec < 0) {
+        phos_status r = R->dr->action(d_perm, S.round, nullptr, 0, R->image, R->image_bytes,
+                                      R->d_present, S.d_status, S.s);
+        if (r) return r;
+    }
+    S.perm_dev = d_perm;
+    S.flags_dev = R->dr->flags();
+    R->in_kernel = true;
+    return PHOS_OK;
+}
+
 extern "C" phos_status phos_restore_after_kernel(phos_restore_t *R, const uint64_t *d_trace,
                                                  uint64_t n_rec, int *misspec) {
     if (!R) return fail(PHOS_EINVAL, "restore_after_kernel: NULL session");
@@ -1202,6 +1342,23 @@ extern "C" phos_status phos_restore_after_kernel(phos_restore_t *R, const uint64
 extern "C" phos_status phos_restore_finish(phos_restore_t *R) {
     if (!R) return fail(PHOS_EINVAL, "restore_finish: NULL session");
     if (R->in_kernel) return fail(PHOS_EINVAL, "restore_finish: inside a kernel round");
+    if (R->dr) {
+        Session &S = R->ss;
+        phos_status r = S.collect(nullptr);
+        if (r) return r;
+        if (R->misspec < 0 && S.flag() >= 0 && (r = restore_rollback(R, S.flag()))) return r;
+        if (R->misspec < 0 &&
+            (r = R->dr->copier(~0ull >> 2, S.round, nullptr, 0, R->image, R->image_bytes,
+                               R->d_present, S.d_status, S.s)))
+            return r;
+        if ((r = S.sync())) return r;
+        uint64_t ctr[6];
+        if ((r = R->dr->collect(S.copier_log, R->od_log, ctr, nullptr))) return r;
+        R->copier_bytes = ctr[2];
+        R->ondemand_bytes = ctr[5];
+        std::fill(R->present.begin(), R->present.end(), 1);
+        return PHOS_OK;
+    }
     if (R->ss.nosync) {
         phos_status r = R->ss.collect(nullptr);
         if (r) return r;

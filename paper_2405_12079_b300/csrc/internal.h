@@ -85,9 +85,45 @@ namespace phos {
 // d_manifest[buf] (PHOS_ECORRUPT in d_status and the lowest bad index in
 // *d_bad on a mismatch).  d_acc (u64[n]) and d_cnt (u32[n]) start zeroed
 // and are left zeroed.  Asynchronous on s.
+// phos_copy whose descriptor count is read on the device (*d_n, at most
+// cap): lists built by device-side decisions.
+phos_status copy_device_count(const phos_table_t *t, const phos_copy_t *d_list, uint32_t cap,
+                              const uint32_t *d_n, void *staging, uint64_t staging_bytes,
+                              const void *image, uint64_t image_bytes, uint32_t *d_present,
+                              uint32_t *d_status, phos_stream_t stream);
 phos_status verify_buffers(const phos_table *t, const std::vector<uint32_t> &bufs,
                            const uint64_t *d_manifest, unsigned long long *d_acc,
                            uint32_t *d_cnt, uint32_t *d_status, int *d_bad, cudaStream_t s);
+// Device-decided protocol rounds (csrc/devround.cu): the copier's pieces
+// and the CoW set / restore need set computed on the device each round.
+struct DevRounds {
+    const phos_table *t = nullptr;
+    uint32_t mode = 0;            // 1 restore, 2 CoW
+    void *mem = nullptr;          // every device array, one allocation
+    uint32_t cap_c = 0;
+    uint64_t cap_lc = 0;
+    alignas(16) unsigned char dev[256];  // the kernels' view of the state
+    phos_status init(const phos_table *t, uint32_t mode, uint64_t chunk,
+                     uint64_t staging_bytes, bool mark_present, cudaStream_t s);
+    // enqueue the copier's move of one round (k_dr_copier + copy engine)
+    phos_status copier(uint64_t quota, uint64_t round, void *staging, uint64_t staging_bytes,
+                       const void *image, uint64_t image_bytes, uint32_t *d_present,
+                       uint32_t *d_status, cudaStream_t s);
+    // enqueue the round's need set (restore) or CoW set (CoW) and its copies
+    phos_status action(const uint8_t *d_perm, uint64_t round, void *staging,
+                       uint64_t staging_bytes, const void *image, uint64_t image_bytes,
+                       uint32_t *d_present, uint32_t *d_status, cudaStream_t s);
+    // every buffer restored / done (after a stop-the-world fallback)
+    phos_status mark_all(cudaStream_t s);
+    const uint8_t *flags() const;
+    // after a synchronisation: the logs (5 u64 per row) and counters
+    // out[0..5] = copier rows, action rows, copier bytes, CoW bytes, direct
+    // bytes, on-demand bytes
+    phos_status collect(std::vector<uint64_t> &copier_log, std::vector<uint64_t> &act_log,
+                        uint64_t out[6], std::vector<uint8_t> *state);
+    ~DevRounds();
+};
+
 }  // namespace phos
 
 struct phos_table {

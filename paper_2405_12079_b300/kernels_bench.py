@@ -163,6 +163,40 @@ def bench_validate_distinct(K, out, reps=5):
                                        violations=int(cnt.cpu().numpy().view(np.uint64)[0]))
 
 
+def bench_emit(K, out):
+    """Validation with the ascending index list (k_validate_emit after
+    k_validate_b) over K concatenated training traces with 1 % stray
+    records, index list capped at 4M entries."""
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(n_kernels=1)
+    lay, rng = cfg["layout"], cfg["rng"]
+    t = phos.Table(lay.base(VA0), lay.size)
+    reads, writes = wl.pick_sets(rng, lay.n)
+    perm = np.zeros(lay.n, np.uint8)
+    perm[reads] = phos.PERM_R
+    perm[writes] = phos.PERM_RW
+    rec, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, 1_300_000, 0.01, 0.0)
+    big = torch.from_numpy(np.tile(rec, K).view(np.uint8)).cuda()
+    N = len(rec) * K
+    cap = 4 << 20
+    d_perm = torch.from_numpy(perm).cuda()
+    bm = torch.empty(((N + 31) // 32) * 4, dtype=torch.uint8, device="cuda")
+    cnt = torch.empty(24, dtype=torch.uint8, device="cuda")
+    vv = torch.empty(256, dtype=torch.uint8, device="cuda")
+    idx = torch.empty(8 * cap, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(4, dtype=torch.uint8, device="cuda")
+
+    def run(with_idx):
+        phos.validate(t, d_perm.data_ptr(), big.data_ptr(), N, 4, bm.data_ptr(), cnt.data_ptr(),
+                      vv.data_ptr(), vv.data_ptr() + 128, idx.data_ptr() if with_idx else None,
+                      cap if with_idx else 0, st.data_ptr(), s)
+    ms_plain = timeit(lambda: run(False))
+    ms_idx = timeit(lambda: run(True))
+    out["validate_with_index_list"] = dict(records=N, violations=int(
+        cnt.cpu().numpy().view(np.uint64)[0]), ms_without=ms_plain, ms_with=ms_idx,
+        emit_ms=ms_idx - ms_plain)
+
+
 def bench_copy(gb, out):
     s = torch.cuda.current_stream().cuda_stream
     G = int(gb) << 30
@@ -260,7 +294,8 @@ def bench_speculate(out, n_launch=20000):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", default="all",
-                    choices=["validate", "validate_distinct", "copy", "speculate", "all"])
+                    choices=["validate", "validate_distinct", "emit", "copy", "speculate",
+                             "all"])
     ap.add_argument("--traces", type=int, default=160)
     ap.add_argument("--copy-gb", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0, help="validate kernel variant (0 = both)")
@@ -270,6 +305,8 @@ def main():
         bench_validate(a.traces, out, (1, 2) if a.variant == 0 else (a.variant,))
     if a.kernel == "validate_distinct":
         bench_validate_distinct(a.traces, out)
+    if a.kernel == "emit":
+        bench_emit(a.traces, out)
     if a.kernel in ("copy", "all"):
         bench_copy(a.copy_gb, out)
     if a.kernel in ("speculate", "all"):

@@ -81,6 +81,8 @@ _SIGS = {
     "phos_server_stats": (_i32, [_vp, _vp]),
     "phos_ckpt_begin": (_i32, [_vp, _vp, _vp, _P(_vp)]),
     "phos_ckpt_advance": (_i32, [_vp, _u64, _P(_c.c_int)]),
+    "phos_ckpt_before_kernel_dev": (_i32, [_vp, _vp]),
+    "phos_restore_before_kernel_dev": (_i32, [_vp, _vp]),
     "phos_ckpt_before_kernel": (_i32, [_vp, _vp]),
     "phos_ckpt_after_kernel": (_i32, [_vp, _vp, _u64, _P(_c.c_int)]),
     "phos_ckpt_finish": (_i32, [_vp]),
@@ -101,6 +103,7 @@ _SIGS = {
 CKPT_COW, CKPT_RECOPY = 1, 2
 CKPT_NO_SYNC = 0x100
 CKPT_CONCURRENT = 0x200
+CKPT_DEVICE = 0x400
 
 
 REQ_CHECKPOINT, REQ_RESTORE = 1, 2
@@ -437,6 +440,10 @@ class Checkpoint:
     def before_kernel(self, perm):
         check(lib().phos_ckpt_before_kernel(self.h, perm.ctypes.data), "ckpt_before_kernel")
 
+    def before_kernel_dev(self, d_perm):
+        """CKPT_DEVICE sessions: the round's perm as a device pointer."""
+        check(lib().phos_ckpt_before_kernel_dev(self.h, d_perm), "ckpt_before_kernel_dev")
+
     def after_kernel(self, d_trace, n_rec):
         check(lib().phos_ckpt_after_kernel(self.h, d_trace, n_rec, _c.byref(self._flag)),
               "ckpt_after_kernel")
@@ -493,6 +500,10 @@ class Restore:
     def before_kernel(self, perm):
         check(lib().phos_restore_before_kernel(self.h, perm.ctypes.data),
               "restore_before_kernel")
+
+    def before_kernel_dev(self, d_perm):
+        """CKPT_DEVICE sessions: the round's perm as a device pointer."""
+        check(lib().phos_restore_before_kernel_dev(self.h, d_perm), "restore_before_kernel_dev")
 
     def after_kernel(self, d_trace, n_rec):
         check(lib().phos_restore_after_kernel(self.h, d_trace, n_rec, _c.byref(self._flag)),

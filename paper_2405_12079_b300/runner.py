@@ -88,9 +88,37 @@ class DeviceProcess:
     @staticmethod
     def _flags(rounds):
         """rounds: "sync" (wait for each validation), "nosync" (rule on the
-        device) or "concurrent" (nosync, copier on its own stream)."""
+        device), "concurrent" (nosync, copier on its own stream) or "device"
+        (every round's decisions on the device, perms from device
+        speculation)."""
         return {"sync": 0, "nosync": phos.CKPT_NO_SYNC,
-                "concurrent": phos.CKPT_CONCURRENT}[rounds]
+                "concurrent": phos.CKPT_CONCURRENT, "device": phos.CKPT_DEVICE}[rounds]
+
+    def device_perms(self):
+        """Every kernel's speculated permissions, computed on the device in
+        one launch (phos_speculate_device): u8 [K][n] device tensor."""
+        if getattr(self, "_d_perms", None) is None:
+            n = max(self.layout.n, 1)
+            launches = [(pk.kern.args, pk.kern.kinds) for pk in self.kernels]
+            words, wk, off = phos.flatten_launch_args(launches)
+            dev = self.arena.device
+            d_w = torch.from_numpy((words if len(words) else np.zeros(1, np.uint64))
+                                   .view(np.uint8).copy()).to(dev)
+            d_k = torch.from_numpy(wk if len(wk) else np.zeros(1, np.uint8)).to(dev)
+            d_o = torch.from_numpy(off.view(np.uint8).copy()).to(dev)
+            d_p = torch.zeros(len(self.kernels) * n, dtype=torch.uint8, device=dev)
+            phos.speculate_device(self.table, d_w.data_ptr(), d_k.data_ptr(), d_o.data_ptr(),
+                                  len(self.kernels), d_p.data_ptr(), None, self.stream())
+            self._d_perms = d_p
+        return self._d_perms
+
+    def _before(self, sess, k, device):
+        pk = self.kernels[k]
+        if device:
+            n = max(self.layout.n, 1)
+            sess.before_kernel_dev(self.device_perms().data_ptr() + k * n)
+        else:
+            sess.before_kernel(pk.speculate(self.table, self.perm))
 
     def run_cow(self, image, quota, chunk, staging=None, staging_bytes=0, rounds="sync"):
         """Soft copy-on-write."""
@@ -116,6 +144,9 @@ class DeviceProcess:
                             staging.data_ptr() if staging is not None else None, staging_bytes, s)
         mark = mark or (lambda name: None)
         pre = "cow" if mode & phos.CKPT_COW else "dirty_marking"
+        device = bool(mode & phos.CKPT_DEVICE)
+        if device:
+            self.device_perms()
         k, misspec = 0, False
         K = len(self.kernels)
         prev, passes = None, 0
@@ -130,7 +161,7 @@ class DeviceProcess:
                     break
             pk = self.kernels[k]
             mark(pre)
-            c.before_kernel(pk.speculate(self.table, self.perm))
+            self._before(c, k, device)
             mark("app_kernel")
             self.run_kernel(k)
             mark("validate")
@@ -180,6 +211,9 @@ class DeviceProcess:
         d_manifest: verify every restored buffer against it (finish raises
         PHOS_ECORRUPT on a mismatch)."""
         s = self.stream()
+        device = rounds == "device"
+        if device:
+            self.device_perms()
         r = phos.Restore(self.table, image.data_ptr(), image.numel(), chunk, 4,
                          d_present.data_ptr() if d_present is not None else None, s,
                          self._flags(rounds),
@@ -190,7 +224,7 @@ class DeviceProcess:
             if r.advance(quota):
                 break
             pk = self.kernels[k]
-            r.before_kernel(pk.speculate(self.table, self.perm))
+            self._before(r, k, device)
             self.run_kernel(k)
             misspec = r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1

@@ -82,14 +82,22 @@ def check_ckpt(w, mode, quota, chunk, staging_bytes=0, rounds="sync"):
         assert got["dirty"].tolist() == exp.dirty
         assert got["stats"]["recopy_bytes"] == exp.stats["recopy_bytes"]
     torch.cuda.synchronize()
-    assert got["kernels_run"] == exp.kernels_run
+    if rounds == "device" and exp.misspec is None:
+        # the host never learns when the device's copier finished, so every
+        # kernel of the sequence ran; those after the end do not touch the
+        # image (every buffer was done)
+        assert got["kernels_run"] == len(w.kernels) >= exp.kernels_run
+        for k in range(exp.kernels_run, got["kernels_run"]):
+            proc.run_kernel(k, w.kernels[k])
+    else:
+        assert got["kernels_run"] == exp.kernels_run
     assert [tuple(int(x) for x in r) for r in got["copier"]] == copier_rows(exp.copier_log)
     assert np.array_equal(img.numpy(), exp.image)
     assert w.live_equal(proc)
     return got, exp
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "device"])
 @pytest.mark.parametrize("mode", ["cow", "recopy"])
 def test_training_image_scaled(mode, rounds):
     """Training-process shape at 1/500 scale (1,000 buffers, ~80 MB,
@@ -97,6 +105,8 @@ def test_training_image_scaled(mode, rounds):
     no-sync rounds (rule on the device, no wait per kernel) and the
     concurrent copier (its own stream, event ordering) give exactly the
     lockstep results."""
+    if mode == "recopy" and rounds == "device":
+        pytest.skip("device-decided rounds are for CoW and restore sessions")
     w, cfg = training_world(wl.SEED0 + 2, 0.002, 200)
     quota = a256(w.dp.image_bytes / 100)
     got, exp = check_ckpt(w, mode, quota, 64 * 1024, staging_bytes=4 << 20, rounds=rounds)
@@ -127,7 +137,7 @@ def test_stray_stores_recopy_nosync(rounds):
     assert got["stats"]["violations"] > 0
 
 
-@pytest.mark.parametrize("rounds", ["nosync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["nosync", "concurrent", "device"])
 def test_stray_stores_cow_nosync_falls_back_at_finish(rounds):
     """CoW without a wait per kernel on the mis-speculating workload: the
     device records the same first mis-speculated round as the oracle; the
@@ -200,7 +210,10 @@ def check_restore(w, quota, chunk, rounds="sync"):
     torch.cuda.synchronize()
     assert got["stats"]["misspec_round"] == (-1 if exp.misspec is None else exp.misspec)
     if exp.misspec is None or rounds == "sync":
-        assert got["kernels_during"] == exp.kernels_during
+        # device-decided rounds: the host never learns when the copier is
+        # done, so every kernel runs inside the session
+        assert got["kernels_during"] == (len(w.kernels) if rounds == "device"
+                                         else exp.kernels_during)
         assert [tuple(int(x) for x in r) for r in got["ondemand"]] == \
             [(int(k), int(i), int(o), int(ln), 0) for k, i, o, ln in exp.ondemand]
         assert [tuple(int(x) for x in r) for r in got["copier"]] == \
@@ -211,7 +224,7 @@ def check_restore(w, quota, chunk, rounds="sync"):
     return got, exp
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "device"])
 def test_large_restore_scaled(rounds):
     """Large-restore shape at small scale: 10,000 buffers, layer-local
     read/write sets, background bulk restore plus on-demand copies."""
@@ -224,7 +237,7 @@ def test_large_restore_scaled(rounds):
     assert len(exp.ondemand) > 0
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "device"])
 def test_restore_stray_load_rolls_back(rounds):
     cfg = wl.training(scale=0.0005, seed=wl.SEED0 + 22, n_kernels=40)
 
@@ -290,3 +303,18 @@ def test_native_driver_equals_oracle(mode, rounds):
     assert [tuple(int(x) for x in r) for r in got["copier"]] == copier_rows(exp.copier_log)
     assert np.array_equal(img.numpy(), exp.image)
     assert w.live_equal(proc)
+
+
+@pytest.mark.parametrize("budget", [0, 1 << 20], ids=["no-staging", "staging-1MiB"])
+def test_device_rounds_cow_staging_pressure(budget):
+    """Device-decided CoW rounds with little or no staging: the device's
+    first-fit allocator and its direct copies to the image give exactly the
+    oracle's CoW list, copier pieces and image."""
+    w, cfg = training_world(wl.SEED0 + 40, 0.001, 120)
+    quota = a256(w.dp.image_bytes / 60)
+    got, exp = check_ckpt(w, "cow", quota, 32 * 1024, staging_bytes=budget, rounds="device")
+    assert len(exp.cow_log) > 0
+    if budget == 0:
+        assert all(e[2] == "D" for e in exp.cow_log)
+    else:
+        assert {e[2] for e in exp.cow_log} == {"S", "D"}

@@ -246,8 +246,9 @@ def test_cancelled_requests_leave_the_others_exact():
     srv = phos.Server(4, staging.data_ptr(), staging.numel(), chunk=64 << 10, dma_min=256 << 10,
                       app_priority=True, window=1 << 20)
     app = torch.cuda.Stream()
+    t0 = time.perf_counter()
     with torch.cuda.stream(app):
-        torch.cuda._sleep(200_000_000)          # >= 98 ms at 2032 MHz
+        torch.cuda._sleep(1_000_000_000)        # >= 0.49 s at 2032 MHz
     srv.app_copy(dev.data_ptr(), src.data_ptr(), src.numel(), app.cuda_stream)
     tks = [w.submit(srv, r) for r in w.reqs]
     # requests 0 (checkpoint) and 1 (restore) are admitted, 9 is queued
@@ -259,6 +260,8 @@ def test_cancelled_requests_leave_the_others_exact():
     cancel = (0, 1, 9)
     for q in cancel:
         srv.cancel(tks[q])
+    t_cancel = time.perf_counter() - t0
+    held = srv.stats()["paused_turns"]
     assert states[9] == 0 and srv.poll(tks[9])["state"] == 4
     srv.drain(60_000)
     app.synchronize()
@@ -277,7 +280,7 @@ def test_cancelled_requests_leave_the_others_exact():
                                   exp_dev[r["dev_off"]:r["dev_off"] + r["lay"].arena_bytes]) or
             not np.array_equal(host[r["host_off"]:r["host_off"] + r["img"]],
                                exp_host[r["host_off"]:r["host_off"] + r["img"]])]
-    assert diff == [], (diff, states)
+    assert diff == [], (diff, states, t_cancel, held, st)
     assert np.array_equal(dev, exp_dev)
     assert np.array_equal(host, exp_host)
     with pytest.raises(phos.PhosError):
