@@ -201,6 +201,12 @@ __global__ void __launch_bounds__(512, 3) k_copy_main(const CopyArgs a) {
     }
 }
 
+size_t copy_scratch_bytes(uint32_t n) {
+    const size_t off_res = align_up(8ull * (n + 1), 256);
+    const size_t off_done = align_up(off_res + sizeof(CopyRes) * (size_t)n, 256);
+    return off_done + 4ull * n;
+}
+
 static uint64_t g_tile = 1ull << 16;  // 64 KiB per CTA work item
 static uint32_t g_ctas_per_sm = 3;
 
@@ -220,7 +226,7 @@ static phos_status launch_copy(const phos_table_t *t, const phos_copy_t *d_list,
     phos_table *T = const_cast<phos_table *>(t);
     const size_t off_res = align_up(8ull * (n + 1), 256);
     const size_t off_done = align_up(off_res + sizeof(CopyRes) * (size_t)n, 256);
-    const size_t need = off_done + 4ull * n;
+    const size_t need = copy_scratch_bytes(n);
     {
         std::lock_guard<std::mutex> g(T->mu);
         r = T->copy_scratch.reserve(need);

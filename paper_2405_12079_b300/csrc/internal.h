@@ -85,6 +85,11 @@ namespace phos {
 // d_manifest[buf] (PHOS_ECORRUPT in d_status and the lowest bad index in
 // *d_bad on a mismatch).  d_acc (u64[n]) and d_cnt (u32[n]) start zeroed
 // and are left zeroed.  Asynchronous on s.
+// Bytes of copy-engine scratch for a launch of n descriptors.
+size_t copy_scratch_bytes(uint32_t n);
+// Descriptors a table's copy scratch holds from creation on (a larger
+// launch grows it, which synchronises the device).
+constexpr uint32_t kCopyReserve = 1024;
 // phos_copy whose descriptor count is read on the device (*d_n, at most
 // cap): lists built by device-side decisions.
 phos_status copy_device_count(const phos_table_t *t, const phos_copy_t *d_list, uint32_t cap,

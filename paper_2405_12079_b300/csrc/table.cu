@@ -166,6 +166,14 @@ extern "C" phos_status phos_table_create(const phos_buf_t *bufs, uint32_t n,
     t->view.fence1 = d + 2 * std::max(n, 1u);
     t->view.fence2 = t->view.fence1 + std::max(nf1, 1u);
     t->view.n = n;
+    // the copy engine's scratch for up to max(n, 1024) descriptors now, so
+    // that copies on this table (a server admitting it, a session's rounds)
+    // never grow it -- growth synchronises the whole device
+    phos_status r = t->copy_scratch.reserve(copy_scratch_bytes(std::max(n, kCopyReserve)));
+    if (r) {
+        phos_table_destroy(t);
+        return r;
+    }
     *out = t;
     return PHOS_OK;
 }

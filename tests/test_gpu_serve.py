@@ -21,25 +21,37 @@ def a256(x):
 class World:
     """Disjoint device and host regions, one per request."""
 
-    def __init__(self, seed, n_req=24, packed=False):
+    def __init__(self, seed, n_req=24, packed=False, buffers=(1, 300), size_hi=(2_000, 60_000)):
         """packed: buffer sizes multiples of 256 with no gaps, so pieces of
-        neighbouring buffers are contiguous on both sides and merge."""
+        neighbouring buffers are contiguous on both sides and merge.
+        buffers: range of buffer counts per request (log-uniform when the
+        range spans more than a factor of 10); size_hi: range of each
+        request's largest buffer size."""
         rng = np.random.default_rng(seed)
         self.rng = rng
-        self.dev_h = rng.integers(0, 256, 96 << 20, dtype=np.uint8)
-        self.host_h = rng.integers(0, 256, 96 << 20, dtype=np.uint8)
-        self.dev = torch.from_numpy(self.dev_h.copy()).cuda()
-        self.host = torch.from_numpy(self.host_h.copy()).pin_memory()
-        self.reqs = []
-        doff = hoff = 0
+        lays = []
         for q in range(n_req):
-            nb = int(rng.integers(1, 300))
-            sizes = wl.sizes_uniform(rng, nb, 1, int(rng.integers(2_000, 60_000)))
+            lo, hi = buffers
+            if hi > 10 * lo:
+                nb = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+            else:
+                nb = int(rng.integers(lo, hi))
+            sizes = wl.sizes_uniform(rng, nb, 1, int(rng.integers(*size_hi)))
             if packed:
                 sizes = (sizes + np.uint64(255)) // np.uint64(256) * np.uint64(256)
                 lay = wl.make_layout(rng, sizes, gap_lo=0, gap_hi=0)
             else:
                 lay = wl.make_layout(rng, sizes, gap_lo=0, gap_hi=2048)
+            lays.append(lay)
+        dev_b = sum(l.arena_bytes + 4096 for l in lays) + 4096
+        host_b = sum(a256(int(sum(a256(x) for x in l.size))) + 4096 for l in lays) + 4096
+        self.dev_h = rng.integers(0, 256, dev_b, dtype=np.uint8)
+        self.host_h = rng.integers(0, 256, host_b, dtype=np.uint8)
+        self.dev = torch.from_numpy(self.dev_h.copy()).cuda()
+        self.host = torch.from_numpy(self.host_h.copy()).pin_memory()
+        self.reqs = []
+        doff = hoff = 0
+        for q, lay in enumerate(lays):
             off = doff
             doff += lay.arena_bytes + 4096
             t = phos.Table(lay.base(self.dev.data_ptr() + off), lay.size)
@@ -78,10 +90,17 @@ class World:
                           a256(r["img"]))
 
 
+@pytest.mark.parametrize("shape", ["small", "cfg4-buffers"])
 @pytest.mark.parametrize("packed", [False, True], ids=["gaps", "packed"])
 @pytest.mark.parametrize("dma_min", [0, 256 << 10], ids=["sm-copies", "dma"])
-def test_alone_and_mix_give_the_same_bytes(dma_min, packed):
-    w = World(5, packed=packed)
+def test_alone_and_mix_give_the_same_bytes(dma_min, packed, shape):
+    """shape cfg4-buffers: the serving workload's 100-10,000 buffers per
+    request (log-uniform), at reduced bytes (buffers of at most 2-8 KB)."""
+    if shape == "small":
+        w = World(5, packed=packed)
+    else:
+        w = World(15, n_req=16, packed=packed, buffers=(100, 10_000), size_hi=(2_000, 8_000))
+        assert max(r["lay"].n for r in w.reqs) > 2000
     exp_dev, exp_host = w.expected()
     cks = [a256(r["img"]) for r in w.reqs if r["kind"] == phos.REQ_CHECKPOINT]
     stg = max(max(cks), sum(cks) // 2)       # smaller than all checkpoints together
