@@ -1011,6 +1011,13 @@ def restore_line(args, world):
 
     stw_restore_ms, stw_total_ms, dig_stw = stw()
     lock = concurrent("sync")
+    # the concurrent session with a copier window of two rounds' quota: the
+    # same pieces and decisions, issued no further ahead than that
+    phos.copier_window(2 * quota)
+    try:
+        win = concurrent("concurrent")
+    finally:
+        phos.copier_window(0)
     clk = Clocks(dev)
     clk.start()
     l0 = phos.launch_count()
@@ -1034,13 +1041,19 @@ def restore_line(args, world):
                            "misspec_round": st["misspec_round"]},
             "stop_the_world": {"restore_ms": stw_restore_ms, "total_ms": stw_total_ms,
                                "first_kernel_ms": stw_restore_ms},
+            "concurrent_copier_window": {
+                "window_bytes": 2 * quota, "total_ms": win[0], "first_kernel_ms": win[1],
+                "stall_p50_ms": float(np.percentile(win[2], 50)),
+                "stall_p99_ms": float(np.percentile(win[2], 99)),
+                "stall_split": stall_split(win[2], win[3]["od_per_kernel"])},
             "lockstep": {"total_ms": lock[0], "first_kernel_ms": lock[1],
                          "stall_p50_ms": float(np.percentile(lock[2], 50)),
                          "stall_p99_ms": float(np.percentile(lock[2], 99))},
             "total_speedup_vs_stop_the_world": stw_total_ms / total,
             "first_kernel_speedup": stw_restore_ms / max(first_ms, 1e-6),
             "verified": {"final_memory_equals_stw_restore_plus_replay":
-                         bool(torch.equal(dig_stw, dig_cc)) and bool(torch.equal(dig_stw, lock[5]))},
+                         bool(torch.equal(dig_stw, dig_cc)) and bool(torch.equal(dig_stw, lock[5]))
+                         and bool(torch.equal(dig_stw, win[5]))},
             "gpu_launches": launches, "clocks": clocks}
     return line
 

@@ -484,6 +484,15 @@ enum { PHOS_CKPT_NO_SYNC = 0x100 };
  * anyway).  Every host decision, and so every result, is the lockstep
  * mode's. */
 enum { PHOS_CKPT_CONCURRENT = 0x200 };
+/* Copier window of PHOS_CKPT_CONCURRENT sessions (process-wide; 0, the
+ * default, = none): before an advance issues the copier's next pieces, the
+ * calling thread waits until at most `bytes` of earlier copier pieces are
+ * still in flight.  Without a window the host may issue the whole image at
+ * once, and a kernel that needs a buffer whose pieces sit deep in the
+ * copier's queue waits for that queue; with one, such pieces are never far
+ * from landing.  The pieces and every decision are unchanged (they depend
+ * on rounds, not on timing); only when the host issues them changes. */
+phos_status phos_copier_window(uint64_t bytes);
 /* OR'ed into mode (CoW sessions) or restore flags (implies
  * PHOS_CKPT_NO_SYNC; not with PHOS_CKPT_CONCURRENT or a manifest): every
  * per-round decision is taken on the device from device-resident state --

@@ -41,6 +41,11 @@ enum : uint8_t { kPending = 0, kInflight = 1, kDone = 2 };
 // on the same link, so large pieces default to the engines.
 static uint64_t g_dma_min = 1ull << 20;
 
+// Copier window of concurrent sessions (phos_copier_window): 0 = the host
+// issues copier batches as fast as the rounds go; else an advance first
+// waits until at most this many bytes of earlier batches are in flight.
+static uint64_t g_copier_window = 0;
+
 // First fit over free extents sorted by offset, coalesced on release.
 struct FirstFit {
     std::vector<std::pair<uint64_t, uint64_t>> free;  // (off, len)
@@ -161,10 +166,15 @@ struct Session {
     cudaStream_t cs = nullptr;
     phos_table_t *tc = nullptr;
     cudaEvent_t app_ev = nullptr;
-    std::deque<std::pair<uint64_t, cudaEvent_t>> bq;   // in flight, ascending
+    struct Batch {
+        uint64_t b, bytes;
+        cudaEvent_t ev;
+    };
+    std::deque<Batch> bq;               // in flight, ascending
     std::vector<cudaEvent_t> ev_free;
     uint64_t batch_done = 0;            // every batch <= this has completed
     uint64_t batch = 0;                 // copier batches issued on cs
+    uint64_t inflight_bytes = 0;        // bytes of the batches in bq
     std::vector<uint64_t> last_batch;   // per buffer: batch of its last piece
 
     phos_status init(const phos_table *tt, cudaStream_t ss, uint32_t ww, uint64_t ch) {
@@ -223,20 +233,35 @@ struct Session {
         return e;
     }
 
-    // Record the event of copier batch b (b = the previous batch + 1) on
-    // the copier stream, retiring the events of completed batches first.
-    phos_status record_batch(uint64_t b) {
+    void retire_front() {
+        batch_done = bq.front().b;
+        inflight_bytes -= bq.front().bytes;
+        ev_free.push_back(bq.front().ev);
+        bq.pop_front();
+    }
+
+    // Retire the batches that have completed; then, with a copier window,
+    // wait (on the host) until at most `window` bytes are in flight.
+    phos_status retire_batches() {
         while (!bq.empty()) {
-            const cudaError_t q = cudaEventQuery(bq.front().second);
+            const cudaError_t q = cudaEventQuery(bq.front().ev);
             if (q == cudaErrorNotReady) {
                 cudaGetLastError();
                 break;
             }
             if (q != cudaSuccess) return cuda_fail(q, "copier batch event");
-            batch_done = bq.front().first;
-            ev_free.push_back(bq.front().second);
-            bq.pop_front();
+            retire_front();
         }
+        while (g_copier_window && inflight_bytes > g_copier_window && !bq.empty()) {
+            PHOS_CUDA(cudaEventSynchronize(bq.front().ev));
+            retire_front();
+        }
+        return PHOS_OK;
+    }
+
+    // Record the event of copier batch b (b = the previous batch + 1, bytes
+    // its payload) on the copier stream.
+    phos_status record_batch(uint64_t b, uint64_t bytes) {
         cudaEvent_t e;
         if (ev_free.empty()) {
             PHOS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -245,7 +270,8 @@ struct Session {
             ev_free.pop_back();
         }
         PHOS_CUDA(cudaEventRecord(e, cs));
-        bq.push_back({b, e});
+        bq.push_back({b, bytes, e});
+        inflight_bytes += bytes;
         batch = b;
         return PHOS_OK;
     }
@@ -253,9 +279,9 @@ struct Session {
     // Make the caller's stream wait for copier batch b (and so for every
     // earlier one).
     phos_status app_wait(uint64_t b) {
-        if (!b || b <= batch_done || bq.empty() || b < bq.front().first) return PHOS_OK;
-        const uint64_t k = std::min<uint64_t>(b - bq.front().first, bq.size() - 1);
-        PHOS_CUDA(cudaStreamWaitEvent(s, bq[k].second, 0));
+        if (!b || b <= batch_done || bq.empty() || b < bq.front().b) return PHOS_OK;
+        const uint64_t k = std::min<uint64_t>(b - bq.front().b, bq.size() - 1);
+        PHOS_CUDA(cudaStreamWaitEvent(s, bq[k].ev, 0));
         return PHOS_OK;
     }
 
@@ -290,7 +316,7 @@ struct Session {
         }
         if (tc) phos_table_destroy(tc);
         if (app_ev) cudaEventDestroy(app_ev);
-        for (auto &be : bq) cudaEventDestroy(be.second);
+        for (auto &be : bq) cudaEventDestroy(be.ev);
         for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
         if (h_up) cudaFreeHost(h_up);
         if (d_up) cudaFree(d_up);
@@ -565,6 +591,11 @@ extern "C" phos_status phos_ckpt_frequency(double n, double f_fail, double o, do
     return PHOS_OK;
 }
 
+extern "C" phos_status phos_copier_window(uint64_t bytes) {
+    g_copier_window = bytes;
+    return PHOS_OK;
+}
+
 extern "C" phos_status phos_host_copy_config(uint64_t dma_min_bytes) {
     g_dma_min = dma_min_bytes;
     return PHOS_OK;
@@ -661,6 +692,8 @@ static phos_status ckpt_advance(phos_ckpt *c, uint64_t quota) {
     // copies); the kernels that follow wait for it only where they write
     const uint64_t b = S.batch + 1;
     if (S.cs) {
+        phos_status r0 = S.retire_batches();
+        if (r0) return r0;
         PHOS_CUDA(cudaEventRecord(S.app_ev, S.s));
         PHOS_CUDA(cudaStreamWaitEvent(S.cs, S.app_ev, 0));
     }
@@ -696,7 +729,9 @@ static phos_status ckpt_advance(phos_ckpt *c, uint64_t quota) {
     phos_status r = S.submit(v, c->staging, c->staging_bytes, c->image, c->image_bytes, nullptr,
                              true);
     if (r) return r;
-    if (S.cs && !v.empty() && (r = S.record_batch(b))) return r;
+    uint64_t vb = 0;
+    for (const phos_copy_t &d : v) vb += d.len;
+    if (S.cs && !v.empty() && (r = S.record_batch(b, vb))) return r;
     return PHOS_OK;
 }
 
@@ -1140,6 +1175,8 @@ static phos_status restore_advance(phos_restore *R, uint64_t quota) {
     std::vector<uint32_t> landed, touched;
     uint64_t b = S.batch + 1, sub_bytes = 0;
     if (S.cs) {
+        phos_status r0 = S.retire_batches();
+        if (r0) return r0;
         PHOS_CUDA(cudaEventRecord(S.app_ev, S.s));
         PHOS_CUDA(cudaStreamWaitEvent(S.cs, S.app_ev, 0));
     }
@@ -1153,7 +1190,7 @@ static phos_status restore_advance(phos_restore *R, uint64_t quota) {
         if ((r = R->verify(landed, S.cs ? S.cs : S.s))) return r;
         if (S.cs) {
             for (uint32_t i : touched) S.last_batch[i] = b;
-            if ((r = S.record_batch(b))) return r;
+            if ((r = S.record_batch(b, sub_bytes))) return r;
             ++b;
         }
         v.clear();

@@ -390,11 +390,18 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     const uint32_t W = p.wpb;
     const uint64_t brec = 32ull * W;
     const uint64_t nbatch = (p.n_rec + brec - 1) / brec;
-    const uint64_t b0 = nbatch * c / G, b1 = nbatch * (c + 1) / G;
+    // Batches go to warps grid-stride (batch bt to global warp bt mod TW),
+    // so at any moment the whole grid reads one contiguous window of the
+    // trace.  Contiguous per-CTA ranges put 148 streams a fixed stride
+    // apart, and some trace lengths mapped that stride badly onto the
+    // memory channels (0.54 against 0.79-0.85 of HBM at neighbouring
+    // lengths, measured).
+    const uint64_t TW = G * nwarps;
+    const uint64_t b1 = nbatch;
     const uint64_t nfull = p.n_rec / brec;
     Lead *mine = leads + 64 * warp;
     Acc acc;
-    uint64_t bt = b0 + warp;
+    uint64_t bt = c * nwarps + warp;
     // Full batches run as one stream per warp: the leader records of the
     // warp's next batch are loaded a batch ahead and the record ring runs on
     // into that batch's first pairs, so no batch begins with a load the warp
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         uint32_t sel = 0;
         const uint32_t half = lane >> 4;
         while (bt < b1 && bt < nfull) {
-            const uint64_t nt = bt + nwarps;
+            const uint64_t nt = bt + TW;
             const bool more = nt < b1 && nt < nfull;
             Lead *ldp = mine + 32 * sel;
             ldp[lane] = make_lead(L, lane < W ? L.lane_search(xl & PHOS_REC_ADDR_MASK) : -1,
@@ -448,7 +455,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         }
     }
     // the trace's last, partial batch (if this warp has it)
-    for (; bt < b1; bt += nwarps) {
+    for (; bt < b1; bt += TW) {
         const uint64_t r0 = bt * brec;
         const uint64_t nb = min(brec, p.n_rec - r0);
         const uint64_t *recs = p.trace + r0;
@@ -535,29 +542,44 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     }
 }
 
-// Ascending list of the first cap violating record indices.
-// units / unit_words: the main kernel's per-CTA partition (CTA c owns
-// units [units*c/G, units*(c+1)/G), each unit_words bitmap words).
+// Ascending list of the first cap violating record indices, in two
+// launches independent of how the validation kernel split the records:
+// k_emit_count counts the violations of each CTA's contiguous range of
+// bitmap words (cnt[4c + 3]), k_validate_emit takes the exclusive prefix of
+// those counts and writes its range's indices with a block scan.
+__global__ void __launch_bounds__(512) k_emit_count(const uint32_t *bitmap, uint64_t nwords,
+                                                   uint64_t *cnt) {
+    __shared__ unsigned long long s_n;
+    const uint64_t G = gridDim.x, c = blockIdx.x;
+    const uint64_t w0 = nwords * c / G, w1 = nwords * (c + 1) / G;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    unsigned long long n = 0;
+    for (uint64_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) n += __popc(bitmap[w]);
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(&s_n, n);
+    __syncthreads();
+    if (threadIdx.x == 0) cnt[4 * c + 3] = s_n;
+}
+
 __global__ void __launch_bounds__(512) k_validate_emit(const uint32_t *bitmap, uint64_t n_rec,
-                                                       uint64_t units, uint32_t unit_words,
-                                                       const uint64_t *cta_cnt, uint64_t *idx,
+                                                       const uint64_t *cnt, uint64_t *idx,
                                                        uint64_t cap) {
     __shared__ unsigned long long s_pre;
     __shared__ uint32_t s_warp[16];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t G = gridDim.x, c = blockIdx.x;
-    if (cta_cnt[c * 4] == 0) return;
+    if (cnt[4 * c + 3] == 0) return;
     if (tid == 0) s_pre = 0;
     __syncthreads();
     unsigned long long pre = 0;
-    for (uint64_t q = tid; q < c; q += blockDim.x) pre += cta_cnt[q * 4];
+    for (uint64_t q = tid; q < c; q += blockDim.x) pre += cnt[4 * q + 3];
     if (pre) atomicAdd(&s_pre, pre);
     __syncthreads();
     uint64_t prefix = s_pre;
     if (prefix >= cap) return;
-    const uint64_t t0 = units * c / G, t1 = units * (c + 1) / G;
     const uint64_t nwords = (n_rec + 31) / 32;
-    const uint64_t w0 = t0 * unit_words, w1 = min(t1 * unit_words, nwords);
+    const uint64_t w0 = nwords * c / G, w1 = nwords * (c + 1) / G;
     for (uint64_t wb = w0; wb < w1; wb += blockDim.x) {
         const uint64_t wi = wb + tid;
         uint32_t v = wi < w1 ? bitmap[wi] : 0u;
@@ -585,6 +607,20 @@ __global__ void __launch_bounds__(512) k_validate_emit(const uint32_t *bitmap, u
         __syncthreads();
         if (prefix >= cap) break;
     }
+}
+
+// Enqueue the index list (both launches) on s.
+static phos_status emit_index_list(const uint32_t *d_bitmap, uint64_t n_rec, uint64_t G,
+                                   uint64_t *cnt, uint64_t *d_idx, uint64_t cap,
+                                   cudaStream_t s) {
+    const uint64_t nwords = (n_rec + 31) / 32;
+    k_emit_count<<<(unsigned)G, 512, 0, s>>>(d_bitmap, nwords, cnt);
+    count_launch();
+    PHOS_CUDA(cudaGetLastError());
+    k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, cnt, d_idx, cap);
+    count_launch();
+    PHOS_CUDA(cudaGetLastError());
+    return PHOS_OK;
 }
 
 struct ValPlan {
@@ -626,20 +662,23 @@ static uint32_t g_val_variant = 0;  // 0 auto, 1 TMA ring, 2 batched leaders
 static uint32_t g_val_wait_limit = kWaitLimit;
 static uint32_t g_val_ctas = 0;     // 0 auto (one per SM), else the grid size
 
-// Words per warp batch: 32 (most amortisation of the leader searches)
-// unless that leaves fewer than two batches per warp of the grid; then 16,
-// then 8, so small traces still occupy every warp.
+// Words per warp batch, W in {32, 16, 8}: the one that minimises the
+// busiest warp's work, words x (W + 6) / W -- each batch costs its leader
+// searches on top of its words, which makes an 8-word batch ~1.45x and a
+// 16-word batch ~1.15x as dear per record as a 32-word one (measured:
+// 260M records took 0.60 ms with 8-word batches, 0.41 ms with 32).  Small
+// traces still spread over every warp; large ones keep W = 32 even where a
+// smaller W would shave a partial batch off the tail.
 static uint32_t words_per_batch(uint64_t n_rec, uint64_t ctas) {
-    // the W in {32, 16, 8} whose busiest warp has the fewest words, the
-    // larger W on a tie (fewer leader searches)
     const uint64_t warps = ctas * (kValThreads / 32);
     uint32_t best = 32;
-    uint64_t best_words = ~0ull;
+    double best_cost = 1e300;
     for (uint32_t W = 32; W >= 8; W /= 2) {
         const uint64_t nb = (n_rec + 32ull * W - 1) / (32ull * W);
         const uint64_t words = (nb + warps - 1) / warps * W;
-        if (words < best_words) {
-            best_words = words;
+        const double cost = (double)words * (W + 6) / W;
+        if (cost < best_cost) {
+            best_cost = cost;
             best = W;
         }
     }
@@ -757,11 +796,8 @@ phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
     count_launch();
     PHOS_CUDA(cudaGetLastError());
     if (d_idx && idx_cap && n_rec) {
-        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, units,
-                                                    (uint32_t)(unit / 32), p.cta_cnt, d_idx,
-                                                    idx_cap);
-        count_launch();
-        PHOS_CUDA(cudaGetLastError());
+        phos_status re = emit_index_list(d_bitmap, n_rec, G, p.cta_cnt, d_idx, idx_cap, s);
+        if (re) return re;
     }
     return PHOS_OK;
 }
@@ -906,10 +942,8 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
     count_launch();
     PHOS_CUDA(cudaGetLastError());
     if (d_idx && idx_cap && n_rec) {
-        k_validate_emit<<<(unsigned)G, 512, 0, s>>>(d_bitmap, n_rec, units, wpb,
-                                                    p.cta_cnt, d_idx, idx_cap);
-        count_launch();
-        PHOS_CUDA(cudaGetLastError());
+        r = emit_index_list(d_bitmap, n_rec, G, p.cta_cnt, d_idx, idx_cap, s);
+        if (r) return r;
     }
     return PHOS_OK;
 }

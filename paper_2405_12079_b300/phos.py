@@ -51,6 +51,7 @@ _SIGS = {
     "phos_validate_grid": (_i32, [_u32]),
     "phos_validate_wait_limit": (_i32, [_u32]),
     "phos_host_copy_config": (_i32, [_u64]),
+    "phos_copier_window": (_i32, [_u64]),
     "phos_ckpt_frequency": (_i32, [_c.c_double, _c.c_double, _c.c_double, _c.c_double,
                                    _c.c_double, _P(_c.c_double), _P(_c.c_double)]),
     "phos_validate_noalloc": (_i32, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _u64,
@@ -351,6 +352,11 @@ def host_copy_config(dma_min_bytes=0):
 
 def copy_config(tile_bytes=0, ctas_per_sm=0):
     return check(lib().phos_copy_config(tile_bytes, ctas_per_sm), "copy_config")
+
+
+def copier_window(nbytes=0):
+    """phos_copier_window: bound the copier bytes in flight (0 = none)."""
+    return check(lib().phos_copier_window(nbytes), "copier_window")
 
 
 def harness_digest(ptrs, lens, d_out, stream=None):

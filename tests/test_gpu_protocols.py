@@ -224,16 +224,25 @@ def check_restore(w, quota, chunk, rounds="sync"):
     return got, exp
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "device"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "concurrent-window",
+                                    "device"])
 def test_large_restore_scaled(rounds):
     """Large-restore shape at small scale: 10,000 buffers, layer-local
-    read/write sets, background bulk restore plus on-demand copies."""
+    read/write sets, background bulk restore plus on-demand copies.  With a
+    copier window the host holds back the copier's next pieces until few
+    are in flight; the decisions, and so the results, do not change."""
     cfg = wl.large_restore(scale=0.0005, n_kernels=150, n_rec=1024)
 
     def mk(rng, lay, va0):
         return wl.make_restore_kernels(rng, lay, va0, cfg["n_kernels"], cfg["n_rec"])
     w = World(cfg["layout"], cfg["seed"], mk)
-    got, exp = check_restore(w, a256(w.dp.image_bytes / 300), 64 * 1024, rounds)
+    quota = a256(w.dp.image_bytes / 300)
+    if rounds == "concurrent-window":
+        phos.copier_window(2 * quota)
+    try:
+        got, exp = check_restore(w, quota, 64 * 1024, rounds.split("-")[0])
+    finally:
+        phos.copier_window(0)
     assert len(exp.ondemand) > 0
 
 
