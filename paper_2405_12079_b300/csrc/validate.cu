@@ -41,7 +41,6 @@ constexpr uint32_t kTileRec = 2048;
 constexpr uint32_t kTileBytes = kTileRec * 8;
 constexpr uint32_t kValThreads = 1024;
 constexpr uint32_t kMaxStages = 8;
-constexpr uint64_t kRsvdMask = 0x3Full << 57;
 constexpr uint32_t kWaitLimit = 1u << 24;   // probes before a tile wait gives up
 
 struct ValParams {
@@ -60,6 +59,7 @@ struct ValParams {
     uint64_t *cta_cnt;  // [grid][4]
     uint32_t *vacc;     // [2][nvw], zero between calls
     uint32_t *ticket;   // zero between calls
+    unsigned long long *next;  // batched variant: next batch to take, zero between calls
     uint32_t w;
     uint32_t nvw;
     uint32_t stages;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     unsigned long long *red = reinterpret_cast<unsigned long long *>(cur);
     uint32_t *last = reinterpret_cast<uint32_t *>(cur + 24);
     cur += 32;
-    const uint32_t nf1 = (n + 31) >> 5, nf2 = (n + 1023) >> 10;
+    const uint32_t nf1 = (n + 31) >> 5;
     Look L;
     L.n = n;
     L.nf1 = nf1;
@@ -390,18 +390,21 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     const uint32_t W = p.wpb;
     const uint64_t brec = 32ull * W;
     const uint64_t nbatch = (p.n_rec + brec - 1) / brec;
-    // Batches go to warps grid-stride (batch bt to global warp bt mod TW),
-    // so at any moment the whole grid reads one contiguous window of the
-    // trace.  Contiguous per-CTA ranges put 148 streams a fixed stride
-    // apart, and some trace lengths mapped that stride badly onto the
-    // memory channels (0.54 against 0.79-0.85 of HBM at neighbouring
-    // lengths, measured).
-    const uint64_t TW = G * nwarps;
+    // Warps take batches from a shared counter, one batch ahead of the one
+    // they work on: fast warps take more.  A static assignment (each CTA a
+    // contiguous range, or batches grid-stride) left warps finishing up to
+    // 60 us apart on a 400 us launch (global-timer stamps per warp), and the
+    // launch waits for the last one.
     const uint64_t b1 = nbatch;
     const uint64_t nfull = p.n_rec / brec;
     Lead *mine = leads + 64 * warp;
     Acc acc;
-    uint64_t bt = c * nwarps + warp;
+    auto grab = [&]() -> uint64_t {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(p.next, 1ull);
+        return __shfl_sync(0xffffffffu, g, 0);
+    };
+    uint64_t bt = grab();
     // Full batches run as one stream per warp: the leader records of the
     // warp's next batch are loaded a batch ahead and the record ring runs on
     // into that batch's first pairs, so no batch begins with a load the warp
@@ -420,9 +423,9 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         }
         uint32_t sel = 0;
         const uint32_t half = lane >> 4;
-        while (bt < b1 && bt < nfull) {
-            const uint64_t nt = bt + TW;
-            const bool more = nt < b1 && nt < nfull;
+        while (bt < nfull) {
+            const uint64_t nt = grab();
+            const bool more = nt < nfull;
             Lead *ldp = mine + 32 * sel;
             ldp[lane] = make_lead(L, lane < W ? L.lane_search(xl & PHOS_REC_ADDR_MASK) : -1,
                                   kSmemTable);
@@ -454,8 +457,8 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
             sel ^= 1;
         }
     }
-    // the trace's last, partial batch (if this warp has it)
-    for (; bt < b1; bt += TW) {
+    // the trace's last, partial batch (if this warp took it)
+    if (bt < b1) {
         const uint64_t r0 = bt * brec;
         const uint64_t nb = min(brec, p.n_rec - r0);
         const uint64_t *recs = p.trace + r0;
@@ -530,6 +533,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         p.count[1] = red[1];
         p.count[2] = red[2];
         *p.ticket = 0;
+        *p.next = 0;
         if (rk) {
             uint64_t *acc = p.rule.acc;
             acc[3] += red[0];
@@ -751,6 +755,7 @@ phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
     p.victim_st = d_victim_st;
     p.status = d_status;
     p.ticket = reinterpret_cast<uint32_t *>(sc);
+    p.next = reinterpret_cast<unsigned long long *>(sc + 8);
     p.vacc = reinterpret_cast<uint32_t *>(sc + off_vacc);
     p.cta_cnt = reinterpret_cast<uint64_t *>(sc + off_cnt);
     p.w = access_bytes;
@@ -844,7 +849,10 @@ static void *g_noalloc_ptr[64];
 __global__ void k_noalloc_clear(uint8_t *scratch, uint32_t nvw) {
     uint32_t *ticket = reinterpret_cast<uint32_t *>(scratch);
     uint32_t *vacc = reinterpret_cast<uint32_t *>(scratch + kNoallocOffVacc);
-    if (threadIdx.x == 0) *ticket = 0;
+    if (threadIdx.x == 0) {
+        *ticket = 0;
+        *reinterpret_cast<unsigned long long *>(scratch + 8) = 0;  // batch counter
+    }
     for (uint32_t i = threadIdx.x; i < 2 * nvw; i += blockDim.x) vacc[i] = 0;
 }
 
@@ -918,6 +926,7 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
     p.victim_st = d_victim_st;
     p.status = d_status;
     p.ticket = reinterpret_cast<uint32_t *>(sc);
+    p.next = reinterpret_cast<unsigned long long *>(sc + 8);
     p.vacc = reinterpret_cast<uint32_t *>(sc + kNoallocOffVacc);
     p.cta_cnt = reinterpret_cast<uint64_t *>(sc + kNoallocOffCnt);
     p.w = access_bytes;
