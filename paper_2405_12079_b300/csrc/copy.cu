@@ -19,8 +19,11 @@
 //     plain stores post straight onto PCIe, and loads from host memory are
 //     hidden behind the grid's bytes in flight.
 //   * Regions whose source and destination share 16-byte alignment take the
-//     vector path with a byte head and tail; otherwise the widest common
-//     unit (8, 4, 2 or 1 bytes) is used.
+//     vector path with a byte head and tail; otherwise the destination is
+//     brought to a 16-byte boundary and each aligned 16-byte store takes its
+//     bytes out of two aligned source vectors with funnel shifts (the
+//     neighbouring vector comes from the next lane by a shuffle, so every
+//     source vector is loaded once).
 //   * Present bits (restore) are set by the CTA that finishes a
 //     descriptor's last tile, after a device-wide fence, so a stream-ordered
 //     reader never sees a bit before its bytes.

@@ -197,6 +197,32 @@ def bench_emit(K, out):
         emit_ms=ms_idx - ms_plain)
 
 
+def bench_copy_misaligned(gb, out):
+    """Device -> device copies of G GB in 4 MB regions whose source is
+    offset from the destination's alignment by 0, 1, 2, 4, 8 or 12 bytes."""
+    s = torch.cuda.current_stream().cuda_stream
+    G = int(gb) << 30
+    nb = 64
+    bs = G // nb
+    live = torch.empty(G + 4096, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(live.data_ptr(), G + 4096, 5, s)
+    tab = phos.Table([live.data_ptr() + i * bs for i in range(nb)], [bs] * nb)
+    stg = torch.empty(G, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    chunk = 4 << 20
+    for delta in (0, 1, 2, 4, 8, 12):
+        rows = []
+        for i in range(nb):
+            for o in range(0, bs - chunk, chunk):
+                rows.append((o + delta, i * bs + o, chunk - 64, i, phos.COPY_LIVE_TO_STAGING))
+        d = torch.from_numpy(np.array(rows, phos.COPY_DTYPE).view(np.uint8)).cuda()
+        moved = sum(r[2] for r in rows)
+        ms = timeit(lambda: phos.cow_copy(tab, d.data_ptr(), len(rows), stg.data_ptr(), G,
+                                          st.data_ptr(), s), 5, 2)
+        out["copy_d2d_src_offset_%d" % delta] = dict(gb=moved / 1e9, ms=ms,
+                                                    gbs_rw=2 * moved / ms / 1e6)
+
+
 def bench_copy(gb, out):
     s = torch.cuda.current_stream().cuda_stream
     G = int(gb) << 30
@@ -294,8 +320,8 @@ def bench_speculate(out, n_launch=20000):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", default="all",
-                    choices=["validate", "validate_distinct", "emit", "copy", "speculate",
-                             "all"])
+                    choices=["validate", "validate_distinct", "emit", "copy", "copy_misaligned",
+                             "speculate", "all"])
     ap.add_argument("--traces", type=int, default=160)
     ap.add_argument("--copy-gb", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0, help="validate kernel variant (0 = both)")
@@ -307,6 +333,8 @@ def main():
         bench_validate_distinct(a.traces, out)
     if a.kernel == "emit":
         bench_emit(a.traces, out)
+    if a.kernel == "copy_misaligned":
+        bench_copy_misaligned(a.copy_gb, out)
     if a.kernel in ("copy", "all"):
         bench_copy(a.copy_gb, out)
     if a.kernel in ("speculate", "all"):

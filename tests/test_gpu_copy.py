@@ -157,6 +157,27 @@ def test_offsets_by_lengths_sweep(kind):
     w.run(np.array(rows, phos.COPY_DTYPE), "copy")
 
 
+@pytest.mark.parametrize("kind", [1, 4])
+def test_misaligned_multi_tile(kind):
+    """Every source/destination alignment pair (16 x 16) on regions of
+    ~70 KB: the funnel-shift path over whole 64 KiB tiles, several warp
+    chunks and a ragged tail, device -> device and pinned host -> device."""
+    w = World(5, n=40, lo=600_000, hi=700_000, staging=20 << 20, image=20 << 20)
+    rng = np.random.default_rng(55)
+    rows, i = [], 0
+    for so in range(16):
+        for do in range(16):
+            ln = 70_000 + int(rng.integers(0, 600))
+            b = i % w.lay.n
+            slot = i // w.lay.n
+            if kind == 1:
+                rows.append((slot * 80_000 + so, i * 80_000 + do, ln, b, kind))
+            else:
+                rows.append((i * 80_000 + so, slot * 80_000 + do, ln, b, kind))
+            i += 1
+    w.run(np.array(rows, phos.COPY_DTYPE), "copy")
+
+
 @pytest.mark.parametrize("tile,ctas", [(4096, 1), (1 << 16, 3), (1 << 20, 8), (16 << 20, 2)])
 def test_tile_and_grid_shapes(tile, ctas):
     w = World(4, n=12, lo=1 << 20, hi=6 << 20, staging=1 << 20, image=80 << 20)
