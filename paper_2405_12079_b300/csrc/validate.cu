@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate(const ValParams p) 
     }
 }
 
-template <bool kSmemTable>
+template <bool kSmemTable, bool kDyn>
 __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -390,21 +390,28 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     const uint32_t W = p.wpb;
     const uint64_t brec = 32ull * W;
     const uint64_t nbatch = (p.n_rec + brec - 1) / brec;
-    // Warps take batches from a shared counter, one batch ahead of the one
-    // they work on: fast warps take more.  A static assignment (each CTA a
+    // kDyn (traces of more batches than the grid has warps): warps take
+    // batches from a shared counter, one batch ahead of the one they work
+    // on, so fast warps take more.  A static assignment (each CTA a
     // contiguous range, or batches grid-stride) left warps finishing up to
     // 60 us apart on a 400 us launch (global-timer stamps per warp), and the
-    // launch waits for the last one.
+    // launch waits for the last one.  Otherwise batches go grid-stride by
+    // the warp's index in the grid, with no atomics: on a 1.3M-record trace
+    // (one batch or none per warp) one atomic per warp on a single address
+    // cost ~5 us.  Either way every batch is taken exactly once.
     const uint64_t b1 = nbatch;
     const uint64_t nfull = p.n_rec / brec;
+    const uint64_t TW = G * (blockDim.x >> 5);
     Lead *mine = leads + 64 * warp;
     Acc acc;
+    uint64_t bt = c * (blockDim.x >> 5) + warp;
     auto grab = [&]() -> uint64_t {
+        if (!kDyn) return bt + TW;
         unsigned long long g = 0;
         if (lane == 0) g = atomicAdd(p.next, 1ull);
         return __shfl_sync(0xffffffffu, g, 0);
     };
-    uint64_t bt = grab();
+    if (kDyn) bt = grab();
     // Full batches run as one stream per warp: the leader records of the
     // warp's next batch are loaded a batch ahead and the record ring runs on
     // into that batch's first pairs, so no batch begins with a load the warp
@@ -693,6 +700,36 @@ static uint32_t words_per_batch(uint64_t n_rec, uint64_t ctas) {
 
 using namespace phos;
 
+namespace {
+
+template <bool T, bool D>
+phos_status launch_b(uint64_t G, size_t smem, cudaStream_t s, const ValParams &p, bool always_attr) {
+    static bool attr_done = false;
+    if (always_attr || !attr_done) {
+        PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_b<T, D>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_done = true;
+    }
+    k_validate_b<T, D><<<(unsigned)G, kValThreads, smem, s>>>(p);
+    return PHOS_OK;
+}
+
+}  // namespace
+
+// The batched kernel with the table in shared memory or not, and batches
+// from the shared counter when the trace has more batches than the grid
+// has warps (else grid-stride, with no atomics).
+static phos_status launch_validate_b(bool smem_table, uint64_t G, size_t smem, cudaStream_t s,
+                                     const ValParams &p, bool always_attr) {
+    const uint64_t brec = 32ull * p.wpb;
+    const bool dyn = G * (kValThreads / 32) < (p.n_rec + brec - 1) / brec;
+    if (smem_table)
+        return dyn ? launch_b<true, true>(G, smem, s, p, always_attr)
+                   : launch_b<true, false>(G, smem, s, p, always_attr);
+    return dyn ? launch_b<false, true>(G, smem, s, p, always_attr)
+               : launch_b<false, false>(G, smem, s, p, always_attr);
+}
+
 extern "C" phos_status phos_validate_config(uint32_t variant) {
     if (variant > 2) return fail(PHOS_EINVAL, "validate_config: variant %u", variant);
     g_val_variant = variant;
@@ -767,7 +804,7 @@ phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
         p.rule = *rule;
         if (rule_fused) *rule_fused = true;
     }
-    static bool attr_done[4] = {false, false, false, false};
+    static bool attr_done[2] = {false, false};
     auto attr = [&](const void *fn, int slot) -> phos_status {
         if (!attr_done[slot]) {
             PHOS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -790,13 +827,7 @@ phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
     } else {
         bool smem_table;
         const size_t smem = plan_batched(t->n, T->device, &smem_table);
-        if (smem_table) {
-            if ((r = attr((const void *)k_validate_b<true>, 2))) return r;
-            k_validate_b<true><<<(unsigned)G, kValThreads, smem, s>>>(p);
-        } else {
-            if ((r = attr((const void *)k_validate_b<false>, 3))) return r;
-            k_validate_b<false><<<(unsigned)G, kValThreads, smem, s>>>(p);
-        }
+        if ((r = launch_validate_b(smem_table, G, smem, s, p, false))) return r;
     }
     count_launch();
     PHOS_CUDA(cudaGetLastError());
@@ -939,15 +970,7 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
     PHOS_CUDA(cudaGetLastError());
     bool smem_table;
     const size_t smem = plan_batched(t->n, t->device, &smem_table);
-    if (smem_table) {
-        PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_b<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        k_validate_b<true><<<(unsigned)G, kValThreads, smem, s>>>(p);
-    } else {
-        PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_b<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        k_validate_b<false><<<(unsigned)G, kValThreads, smem, s>>>(p);
-    }
+    if ((r = launch_validate_b(smem_table, G, smem, s, p, true))) return r;
     count_launch();
     PHOS_CUDA(cudaGetLastError());
     if (d_idx && idx_cap && n_rec) {

@@ -197,3 +197,25 @@ def test_ring_wait_that_runs_out_reports_etimedout(variant):
         phos.validate_wait_limit()
     assert got["status"] == phos.PHOS_ETIMEDOUT
     check(t, base, lay.size, perm, rec, 4)
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 148])
+def test_batch_assignment_around_one_batch_per_warp(ctas):
+    """Trace lengths around one warp batch per warp of the grid (32 warps per
+    CTA, batches of 256 to 1024 records): the batched kernel takes batches
+    grid-stride when there are no more batches than warps and from the
+    shared counter otherwise; either way every batch is checked once."""
+    rng, lay, base, t = layout_table(64, 80 + ctas, hi=1 << 20)
+    reads, writes = wl.pick_sets(rng, 64, 1, 20)
+    perm = np.zeros(64, np.uint8)
+    perm[reads] = phos.PERM_R
+    perm[writes] = phos.PERM_RW
+    phos.validate_grid(ctas)
+    try:
+        tw = 32 * ctas
+        for brec in (256, 512, 1024):
+            for n_rec in (tw * brec - 33, tw * brec, tw * brec + 1, tw * brec + brec + 5):
+                rec, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, n_rec, 0.002, 0.3)
+                check(t, base, lay.size, perm, rec, 4, idx_cap=5_000)
+    finally:
+        phos.validate_grid(0)
