@@ -27,6 +27,10 @@
 //   * Present bits (restore) are set by the CTA that finishes a
 //     descriptor's last tile, after a device-wide fence, so a stream-ordered
 //     reader never sees a bit before its bytes.
+#include <string.h>
+
+#include <algorithm>
+
 #include "copy_dev.cuh"
 #include "internal.h"
 
@@ -258,6 +262,80 @@ static phos_status launch_copy(const phos_table_t *t, const phos_copy_t *d_list,
     PHOS_CUDA(cudaGetLastError());
     const unsigned G = (unsigned)(sm_count(T->device) * g_ctas_per_sm);
     k_copy_main<<<G, 512, 0, s>>>(a);
+    count_launch();
+    PHOS_CUDA(cudaGetLastError());
+    return PHOS_OK;
+}
+
+// Small host -> device uploads without a device-side read of host memory.
+// While the copier's device -> host DMA copies fill the link, anything the
+// device has to fetch from host memory at run time waits behind them: a
+// cudaMemcpyAsync of 2 KB took ~60 us on B300 (~3 us idle), and SM loads
+// from mapped pinned memory stalled the same way.  Kernel parameters travel
+// with the launch, which the front end fetches ahead of execution, so
+// bytes up to a parameter block go as the parameters of k_put; larger
+// uploads fall back to k_pull (SM loads from the mapped arena).
+template <uint32_t kData>
+struct PutArgs {
+    uint8_t *dst;
+    uint64_t len;
+    uint8_t data[kData];
+};
+
+template <uint32_t kData>
+__global__ void __launch_bounds__(256) k_put(const __grid_constant__ PutArgs<kData> a) {
+    const uint64_t n = a.len;
+    uint64_t done = 0;
+    // 8-byte units (data sits 16 bytes into a block of 8-byte alignment)
+    if (((uintptr_t)a.dst & 7) == 0) {
+        const uint64_t nv = n / 8;
+        const uint64_t *s = reinterpret_cast<const uint64_t *>(a.data);
+        uint64_t *d = reinterpret_cast<uint64_t *>(a.dst);
+        for (uint64_t i = threadIdx.x; i < nv; i += blockDim.x) d[i] = s[i];
+        done = nv * 8;
+    }
+    for (uint64_t i = done + threadIdx.x; i < n; i += blockDim.x) a.dst[i] = a.data[i];
+}
+
+__global__ void __launch_bounds__(256) k_pull(uint8_t *dst, const uint8_t *src, uint64_t n) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t done = 0;
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+        const uint64_t nv = n / 16;
+        const uint4 *s = reinterpret_cast<const uint4 *>(src);
+        uint4 *d = reinterpret_cast<uint4 *>(dst);
+        // volatile loads: a line of host memory seen before is fetched again
+        for (uint64_t i = tid; i < nv; i += nt) d[i] = __ldcv(s + i);
+        done = nv * 16;
+    }
+    for (uint64_t i = done + tid; i < n; i += nt) dst[i] = (uint8_t)__ldcv(src + i);
+}
+
+// The parameter blocks: 4 KB (the classic limit) and 32 KB (the limit of
+// CUDA 12.1 and later), less the header.
+constexpr uint32_t kPutSmall = 4096 - 16, kPutLarge = 32752 - 16;
+
+template <uint32_t kData>
+static phos_status put_launch(void *d_dst, const void *h_src, uint64_t bytes, cudaStream_t s) {
+    PutArgs<kData> a;
+    a.dst = static_cast<uint8_t *>(d_dst);
+    a.len = bytes;
+    memcpy(a.data, h_src, bytes);
+    k_put<kData><<<1, 256, 0, s>>>(a);
+    count_launch();
+    PHOS_CUDA(cudaGetLastError());
+    return PHOS_OK;
+}
+
+phos_status push_small(void *d_dst, const void *h_src, const void *h_src_dev, uint64_t bytes,
+                       cudaStream_t s) {
+    if (!bytes) return PHOS_OK;
+    if (bytes <= kPutSmall) return put_launch<kPutSmall>(d_dst, h_src, bytes, s);
+    if (bytes <= kPutLarge) return put_launch<kPutLarge>(d_dst, h_src, bytes, s);
+    const uint64_t ctas = std::min<uint64_t>((bytes + 16 * 256 * 4 - 1) / (16 * 256 * 4), 64);
+    k_pull<<<(unsigned)ctas, 256, 0, s>>>(static_cast<uint8_t *>(d_dst),
+                                           static_cast<const uint8_t *>(h_src_dev), bytes);
     count_launch();
     PHOS_CUDA(cudaGetLastError());
     return PHOS_OK;

@@ -125,13 +125,16 @@ struct Session {
     cudaStream_t s = nullptr;
     uint32_t n = 0, w = 4;
     uint64_t chunk = 4ull << 20;
-    // pinned host arena for copy lists (recycled at synchronisations)
+    // pinned host arena for copy lists (recycled at synchronisations); the
+    // host arenas are mapped and reach the device by push_small
     phos_copy_t *h_list = nullptr;
+    const phos_copy_t *h_list_dev = nullptr;
     size_t h_cap = 0, h_used = 0;
     phos_copy_t *d_list = nullptr;
     size_t d_cap = 0;
     // validator I/O
     uint8_t *h_perm = nullptr, *d_perm = nullptr;
+    const uint8_t *h_perm_dev = nullptr;
     uint32_t *d_bitmap = nullptr;
     uint64_t bitmap_words = 0;
     uint64_t *h_count = nullptr;      // pinned mapped: count[3]
@@ -153,6 +156,7 @@ struct Session {
     // device-decided rounds: the round's perm and rule flags on the device
     const uint8_t *perm_dev = nullptr, *flags_dev = nullptr;
     uint8_t *h_up = nullptr, *d_up = nullptr;
+    const uint8_t *h_up_dev = nullptr;  // h_up's device-mapped address
     size_t up_cap = 0, up_used = 0, slot = 0;
     uint64_t *d_acc = nullptr;      // u64[8], see k_rule
     uint32_t *d_vic = nullptr;      // victim | victim_st
@@ -186,7 +190,8 @@ struct Session {
         state.assign(n, kPending);
         copied.assign(n, 0);
         const uint32_t nvw = (n + 31) / 32;
-        PHOS_CUDA(cudaHostAlloc(&h_perm, std::max(n, 1u), cudaHostAllocDefault));
+        PHOS_CUDA(cudaHostAlloc(&h_perm, std::max(n, 1u), cudaHostAllocMapped));
+        PHOS_CUDA(cudaHostGetDevicePointer((void **)&h_perm_dev, h_perm, 0));
         PHOS_CUDA(cudaMalloc(&d_perm, std::max(n, 1u)));
         PHOS_CUDA(cudaHostAlloc(&h_count, 64, cudaHostAllocMapped));
         PHOS_CUDA(cudaHostAlloc(&h_victim, 8ull * std::max(nvw, 1u), cudaHostAllocMapped));
@@ -298,7 +303,8 @@ struct Session {
                 h_up = nullptr;
                 d_up = nullptr;
                 const size_t cap = std::max<size_t>({bytes * 64, 2 * up_cap, 1 << 20});
-                PHOS_CUDA(cudaHostAlloc(&h_up, cap, cudaHostAllocDefault));
+                PHOS_CUDA(cudaHostAlloc(&h_up, cap, cudaHostAllocMapped));
+                PHOS_CUDA(cudaHostGetDevicePointer((void **)&h_up_dev, h_up, 0));
                 PHOS_CUDA(cudaMalloc(&d_up, cap));
                 up_cap = cap;
             }
@@ -343,7 +349,8 @@ struct Session {
             cudaFree(d_list);
             h_used = 0;
         }
-        PHOS_CUDA(cudaHostAlloc(&h_list, cap * sizeof(phos_copy_t), cudaHostAllocDefault));
+        PHOS_CUDA(cudaHostAlloc(&h_list, cap * sizeof(phos_copy_t), cudaHostAllocMapped));
+        PHOS_CUDA(cudaHostGetDevicePointer((void **)&h_list_dev, h_list, 0));
         PHOS_CUDA(cudaMalloc(&d_list, cap * sizeof(phos_copy_t)));
         h_cap = d_cap = cap;
         return PHOS_OK;
@@ -410,8 +417,9 @@ struct Session {
         phos_copy_t *hp = h_list + h_used;
         phos_copy_t *dp = d_list + h_used;
         memcpy(hp, v.data(), v.size() * sizeof(phos_copy_t));
-        PHOS_CUDA(cudaMemcpyAsync(dp, hp, v.size() * sizeof(phos_copy_t), cudaMemcpyHostToDevice,
-                                  st));
+        phos_status rp = push_small(dp, hp, h_list_dev + h_used, v.size() * sizeof(phos_copy_t),
+                                    st);
+        if (rp) return rp;
         h_used += v.size();
         return phos_copy(tt, dp, (uint32_t)v.size(), staging, staging_bytes,
                          const_cast<void *>(image), image_bytes, present, d_status, st);
@@ -438,7 +446,8 @@ struct Session {
         }
         if (n) {
             memcpy(h_perm, perm, n);
-            PHOS_CUDA(cudaMemcpyAsync(d_perm, h_perm, n, cudaMemcpyHostToDevice, s));
+            phos_status r = push_small(d_perm, h_perm, h_perm_dev, n, s);
+            if (r) return r;
         }
         return PHOS_OK;
     }
@@ -446,7 +455,8 @@ struct Session {
     phos_status upload_slot(const std::vector<uint8_t> &flags) {
         if (!n) return PHOS_OK;
         memcpy(h_up + slot + n, flags.data(), n);
-        PHOS_CUDA(cudaMemcpyAsync(d_up + slot, h_up + slot, 2ull * n, cudaMemcpyHostToDevice, s));
+        phos_status r = push_small(d_up + slot, h_up + slot, h_up_dev + slot, 2ull * n, s);
+        if (r) return r;
         return PHOS_OK;
     }
 

@@ -96,6 +96,12 @@ phos_status copy_device_count(const phos_table_t *t, const phos_copy_t *d_list, 
                               const uint32_t *d_n, void *staging, uint64_t staging_bytes,
                               const void *image, uint64_t image_bytes, uint32_t *d_present,
                               uint32_t *d_status, phos_stream_t stream);
+// Upload bytes from pinned host memory to device memory on s without the
+// copy engines: up to 32 KB as kernel parameters (copied from h_src at the
+// call), more by SM loads through h_src_dev (h_src's device-mapped
+// address, which must stay unchanged until the upload has run).
+phos_status push_small(void *d_dst, const void *h_src, const void *h_src_dev, uint64_t bytes,
+                       cudaStream_t s);
 phos_status verify_buffers(const phos_table *t, const std::vector<uint32_t> &bufs,
                            const uint64_t *d_manifest, unsigned long long *d_acc,
                            uint32_t *d_cnt, uint32_t *d_status, int *d_bad, cudaStream_t s);

@@ -99,7 +99,8 @@ struct phos_server {
     uint32_t app_pending[2] = {0, 0};           // being issued (h2d, d2h)
     phos_server_stats_t st{};
     // device descriptor rings per direction (pinned staging of lists)
-    phos_copy_t *h_ring[3] = {nullptr, nullptr, nullptr};
+    phos_copy_t *h_ring[3] = {nullptr, nullptr, nullptr};         // pinned, mapped
+    const phos_copy_t *h_ring_dev[3] = {nullptr, nullptr, nullptr}; // their device addresses
     phos_copy_t *d_ring[3] = {nullptr, nullptr, nullptr};
     uint32_t *d_status = nullptr;
     size_t ring_cap = 65536;
@@ -157,8 +158,10 @@ struct phos_server {
         phos_copy_t *hp = h_ring[r] + ring_pos[r];
         phos_copy_t *dp = d_ring[r] + ring_pos[r];
         memcpy(hp, v.data(), v.size() * sizeof(phos_copy_t));
-        PHOS_CUDA(cudaMemcpyAsync(dp, hp, v.size() * sizeof(phos_copy_t), cudaMemcpyHostToDevice,
-                                  s));
+        // not by the copy engines: an upload would queue behind the DMA legs
+        phos_status rp = push_small(dp, hp, h_ring_dev[r] + ring_pos[r],
+                                    v.size() * sizeof(phos_copy_t), s);
+        if (rp) return rp;
         ring_pos[r] += v.size();
         return phos_copy(t, dp, (uint32_t)v.size(), d.d_staging, d.staging_bytes, img, img_bytes,
                          nullptr, d_status, s);
@@ -430,7 +433,9 @@ extern "C" phos_status phos_server_start(const phos_server_desc_t *d, phos_serve
     }
     for (int r = 0; r < 3; ++r) {
         if ((e = cudaHostAlloc(&S->h_ring[r], S->ring_cap * sizeof(phos_copy_t),
-                               cudaHostAllocDefault)) != cudaSuccess ||
+                               cudaHostAllocMapped)) != cudaSuccess ||
+            (e = cudaHostGetDevicePointer((void **)&S->h_ring_dev[r], S->h_ring[r], 0)) !=
+                cudaSuccess ||
             (e = cudaMalloc(&S->d_ring[r], S->ring_cap * sizeof(phos_copy_t))) != cudaSuccess) {
             delete S;
             return cuda_fail(e, "server_start: rings");
