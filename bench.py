@@ -274,7 +274,7 @@ def run_gpu(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     s = torch.cuda.current_stream().cuda_stream
-    phos.host_copy_config(1 << 20 if args.host_copy == "dma" else 0)
+    phos.host_copy_config(args.dma_min if args.host_copy == "dma" else 0)
     scale = args.scale
     cfg = wl.training(scale=scale, n_kernels=200)
     rng, lay = cfg["rng"], cfg["layout"]
@@ -524,8 +524,9 @@ def run_gpu(args, rank, world):
     if rank == 0:
         cpu = cpu_baseline(moved_per_step=tot_moved / args.steps / world,
                            recs_per_step=tot_recs / args.steps / world)
-        legs = ("DMA engines (cudaMemcpyAsync) for pieces >= 1 MiB, k_copy_main for smaller "
-                "ones" if args.host_copy == "dma" else "k_copy_main (SM-issued stores)")
+        legs = ("DMA engines (cudaMemcpyAsync) for pieces >= %d KiB, k_copy_main for smaller "
+                "ones" % (args.dma_min >> 10) if args.host_copy == "dma"
+                else "k_copy_main (SM-issued stores)")
         roof = {"kernel": "host legs of the background copier and recopy, device -> pinned "
                           "host: " + legs + (
                               "; whole step (copier concurrent on its own stream)"
@@ -544,8 +545,8 @@ def run_gpu(args, rank, world):
                        "buffers": lay.n, "kernels": len(dp.kernels),
                        "records_per_kernel": dp.kernels[0].n_rec, "quota": quota,
                        "chunk": chunk, "staging_bytes": staging_bytes,
-                       "host_legs": ("DMA engines for pieces >= 1 MiB" if args.host_copy == "dma"
-                                     else "SM copy kernel"),
+                       "host_legs": ("DMA engines for pieces >= %d KiB" % (args.dma_min >> 10)
+                                     if args.host_copy == "dma" else "SM copy kernel"),
                        "rounds": {"sync": "host waits for each kernel's validation",
                                   "nosync": "no wait per kernel, validation rule on the device",
                                   "concurrent": "no wait per kernel, copier on its own stream "
@@ -911,6 +912,7 @@ def restore_line(args, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     s = torch.cuda.current_stream().cuda_stream
+    phos.host_copy_config(args.dma_min)
     sc = 0.5 * args.scale                      # 60 GB at --scale 1
     cfg = wl.large_restore(scale=sc, n_kernels=500, n_rec=65536)
     rng, lay = cfg["rng"], cfg["layout"]
@@ -1320,7 +1322,7 @@ def run_rounds(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     s = torch.cuda.current_stream().cuda_stream
-    phos.host_copy_config(1 << 20)
+    phos.host_copy_config(args.dma_min)
     n_k = 400
     cfg = wl.training(scale=0.25 * args.scale, n_kernels=n_k)
     rng, lay = cfg["rng"], cfg["layout"]
@@ -1437,7 +1439,11 @@ def main():
                              "priority", "rounds"],
                     help="training: the headline checkpoint step; batched: the 64-image plan")
     ap.add_argument("--host-copy", default="dma", choices=["sm", "dma"],
-                    help="host legs on the SM copy kernel, or pieces >= 1 MiB on the DMA engines")
+                    help="host legs on the SM copy kernel, or pieces >= --dma-min bytes on the "
+                         "DMA engines")
+    ap.add_argument("--dma-min", type=int, default=256 << 10,
+                    help="smallest host-leg piece for the DMA engines (smaller ones: SM copy "
+                         "kernel)")
     ap.add_argument("--rounds", default="concurrent", choices=["sync", "nosync", "concurrent"],
                     help="nosync: protocol rounds do not wait for validation (device-side "
                          "rule); concurrent: also the copier on its own stream")

@@ -437,8 +437,10 @@ phos_status phos_server_stats(phos_server_t *s, phos_server_stats_t *out);
  * from the image) and are at least dma_min_bytes long go to the DMA copy
  * engines (cudaMemcpyAsync, one call per piece, as the paper's prototype
  * copies, Sec. 5) instead of the SM copy kernel; 0 keeps every piece on
- * the SM copy kernel.  Default 1 MiB (the engines move 57 GB/s of payload
- * over this link, SM stores 53 GB/s).  Process-wide. */
+ * the SM copy kernel.  Default 256 KiB: the engines move 57 GB/s of
+ * payload over this link against 53 GB/s for SM stores, and a sub-MiB
+ * piece left to the SM kernel costs a copy launch pair on the copier's
+ * stream.  Process-wide. */
 phos_status phos_host_copy_config(uint64_t dma_min_bytes);
 
 /* ------------------------------------------------- protocol control plane

@@ -38,8 +38,11 @@ enum : uint8_t { kPending = 0, kInflight = 1, kDone = 2 };
 // (cudaMemcpyAsync) instead of the SM copy kernel; 0 = never.  SM-issued
 // stores reach the host in small PCIe write packets (measured 12 % link
 // overhead, 52.8 GB/s of payload) while the copy engines deliver 57.3 GB/s
-// on the same link, so large pieces default to the engines.
-static uint64_t g_dma_min = 1ull << 20;
+// on the same link.  With 5 MB copier batches a 1 MiB threshold left each
+// batch's sub-MiB remainder to a copy launch pair on the copier stream
+// (47.8 GB/s for the copier alone); from 256 KiB up the engines take it
+// (55.5 GB/s), and pieces below it stay batched in one launch.
+static uint64_t g_dma_min = 256ull << 10;
 
 // Copier window of concurrent sessions (phos_copier_window): 0 = the host
 // issues copier batches as fast as the rounds go; else an advance first

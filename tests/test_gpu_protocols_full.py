@@ -5,7 +5,7 @@ them, and regenerates them piece by piece to compare).
   * training-process image (Sec. 4.2 soft CoW, then Sec. 4.3 soft recopy
     on the memory the first checkpoint left): 1,000 buffers, 40 GB, 200
     kernels, 4 MB pieces, copier quota image/100 per round, 2 GB staging,
-    DMA host legs for pieces >= 1 MiB, the copier on its own stream -- the
+    DMA host legs for pieces >= 256 KiB, the copier on its own stream -- the
     benchmark's step.  Traces are shortened to 16,384 records per kernel
     (only the strays, which are loads here, can change a decision, and the
     oracle's validation is a linear scan).
@@ -78,7 +78,7 @@ def arena_mismatches(mem, arena):
 
 @pytest.fixture
 def dma_host_legs():
-    phos.host_copy_config(1 << 20)
+    phos.host_copy_config(256 << 10)
     yield
     phos.host_copy_config(0)
 
