@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     // contiguous range, or batches grid-stride) left warps finishing up to
     // 60 us apart on a 400 us launch (global-timer stamps per warp), and the
     // launch waits for the last one.  Otherwise batches go grid-stride by
-    // the warp's index in the grid, with no atomics: on a 1.3M-record trace
+    // the warp's index in the grid (CTA-minor), with no atomics: on a 1.3M-record trace
     // (one batch or none per warp) one atomic per warp on a single address
     // cost ~5 us.  Either way every batch is taken exactly once.
     const uint64_t b1 = nbatch;
@@ -404,7 +404,9 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
     const uint64_t TW = G * (blockDim.x >> 5);
     Lead *mine = leads + 64 * warp;
     Acc acc;
-    uint64_t bt = c * (blockDim.x >> 5) + warp;
+    // CTA-minor: batch b goes to CTA b % G, so a trace of fewer batches
+    // than warps spreads over every CTA instead of filling the first ones
+    uint64_t bt = (uint64_t)warp * G + c;
     auto grab = [&]() -> uint64_t {
         if (!kDyn) return bt + TW;
         unsigned long long g = 0;
@@ -680,6 +682,15 @@ static uint32_t g_val_ctas = 0;     // 0 auto (one per SM), else the grid size
 // 260M records took 0.60 ms with 8-word batches, 0.41 ms with 32).  Small
 // traces still spread over every warp; large ones keep W = 32 even where a
 // smaller W would shave a partial batch off the tail.
+// CTAs of a batched launch: one per 8 batches up to the SM count.  A CTA's
+// prologue (table and perms into shared memory) and its part in the
+// last-CTA reduction cost the same whether it has one busy warp or 32, and
+// short traces are latency-bound per warp: a 65,536-record trace (256
+// batches) measured 8.7 us on 32 CTAs against 10.3 us on 148.
+static uint64_t batched_grid(uint64_t units, uint64_t ctas) {
+    return std::max<uint64_t>(1, std::min<uint64_t>(ctas, (units + 7) / 8));
+}
+
 static uint32_t words_per_batch(uint64_t n_rec, uint64_t ctas) {
     const uint64_t warps = ctas * (kValThreads / 32);
     uint32_t best = 32;
@@ -770,7 +781,8 @@ phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
     const uint32_t wpb = words_per_batch(n_rec, (uint64_t)sms);
     const uint64_t unit = variant == 1 ? kTileRec : 32ull * wpb;
     const uint64_t units = (n_rec + unit - 1) / unit;
-    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms, units));
+    const uint64_t G = variant == 1 ? std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sms, units))
+                                    : batched_grid(units, (uint64_t)sms);
     const uint32_t nvw = (t->n + 31) / 32;
     const size_t off_vacc = 256, off_cnt = align_up(off_vacc + 8ull * std::max(nvw, 1u), 256);
     const size_t need = off_cnt + 32ull * (size_t)sms;
@@ -943,7 +955,7 @@ extern "C" phos_status phos_validate_noalloc(const phos_table_t *t, const uint8_
         std::min<uint64_t>((uint64_t)sm_count(t->device), kNoallocMaxCtas);
     const uint32_t wpb = words_per_batch(n_rec, ctas);
     const uint64_t units = (n_rec + 32ull * wpb - 1) / (32ull * wpb);
-    const uint64_t G = std::max<uint64_t>(1, std::min<uint64_t>(ctas, units));
+    const uint64_t G = batched_grid(units, ctas);
     const uint32_t nvw = (t->n + 31) / 32;
     ValParams p;
     p.tab = t->view;
