@@ -37,6 +37,14 @@ WORKLOAD = ("training-process image: 1,000 buffers, log-normal 256 B-512 MB, 40 
             "trace per kernel (0.1% stray); soft CoW then soft recopy, copier quota "
             "image/100 per kernel round, 4 MB pieces, 2 GB staging, pinned host image")
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the roofline
+# kernels, from single-launch ncu captures of the current kernels: one
+# 1.3M-record trace, the 260M-record launch over 200 distinct traces, and the
+# device -> device copy's bytes over its algorithmic read + write bytes
+TRAFFIC_ONE_TRACE = 10490880 + 512              # profiles/validate_b_one_trace_1p3M.md
+TRAFFIC_260M = 2.085962e9 + 32.033536e6         # profiles/validate_b_distinct_traces_260M.md
+TRAFFIC_COPY_D2D_RATIO = (1879184896 + 1832464128) / (2 * 1879019520.0)  # copy_main_d2d_2GB.md
+
 
 def a256(x):
     return int(math.ceil(x / 256.0)) * 256
@@ -469,24 +477,36 @@ def run_gpu(args, rank, world):
     val_recs = sum(p.n_rec for p in dp.kernels)
     val_launch_us = 1e3 * val_ms / len(dp.kernels)
     val_gbs = val_recs * 8.125 / (val_ms * 1e6)
+    # L2 flush before each single-launch repetition: a 256 MB write, then a
+    # 256 MB read of another buffer, so that L2 holds clean lines of neither
+    # input (a write alone leaves ~126 MB of dirty lines that the timed
+    # launch would write back: ~6 us on these launches)
+    flw = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flr = torch.ones(256 << 20, dtype=torch.uint8, device="cuda")
+    fl_acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def flushed_ms(fn, reps=5):
+        best = 1e30
+        for _ in range(reps):
+            flw.zero_()
+            torch.sum(flr.view(torch.int64), dim=(0,), out=fl_acc[0])
+            best = min(best, ev_ms(fn, reps=1))
+        return best
     cat = torch.cat([p.d_trace for p in dp.kernels[:50]])
     cat_n = cat.numel() // 8
     # the union of the 50 kernels' speculated sets, so that only the
     # strays violate (as in the per-kernel launches)
     uperm = torch.stack(perms[:50]).max(dim=0).values.contiguous()
-    cat_ms = ev_ms(lambda: phos.validate(dp.table, uperm.data_ptr(), cat.data_ptr(), cat_n, 4,
-                                         bm.data_ptr(), cnt.data_ptr(), vv.data_ptr(),
-                                         vv.data_ptr() + 4 * nvw, None, 0, stw.data_ptr(), s))
+    cat_ms = flushed_ms(lambda: phos.validate(dp.table, uperm.data_ptr(), cat.data_ptr(), cat_n,
+                                              4, bm.data_ptr(), cnt.data_ptr(), vv.data_ptr(),
+                                              vv.data_ptr() + 4 * nvw, None, 0, stw.data_ptr(),
+                                              s))
     cat_gbs = cat_n * 8.125 / (cat_ms * 1e6)
     del cat
-    # the 260M-record launch, L2 flushed (a 256 MB write) before each repetition
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    all_ms = 1e30
-    for _ in range(5):
-        flush.zero_()
-        all_ms = min(all_ms, ev_ms(val_all, reps=1))
+    # the 260M-record launch
+    all_ms = flushed_ms(val_all)
     all_gbs = all_n * 8.125 / (all_ms * 1e6)
-    del all_tr, flush
+    del all_tr, flw, flr
     # CoW copy kernel alone: the step's largest buffers live -> staging
     order = np.argsort(-lay.size.astype(np.int64))
     rows, off = [], 0
@@ -561,28 +581,30 @@ def run_gpu(args, rank, world):
                 {"kernel": "k_validate_b, one launch per kernel trace (1.3M records)",
                  "bound": "hbm", "achieved": val_gbs, "peak": hbm, "unit": "GB/s",
                  "frac": val_gbs / hbm,
-                 "traffic": 10.488064e6 * (val_recs / len(dp.kernels)) / 1.3e6,
+                 "traffic": TRAFFIC_ONE_TRACE * (val_recs / len(dp.kernels)) / 1.3e6,
                  "accesses_per_s": val_recs / (val_ms * 1e-3), "avg_launch_us": val_launch_us,
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                  "traffic_source": "profiles/validate_b_one_trace_1p3M.md (ncu DRAM bytes of "
                                    "one 1.3M-record launch), scaled by records"},
                 {"kernel": "k_validate_b, one launch over 50 traces (65M records, union of "
-                           "their speculated sets)",
+                           "their speculated sets, L2 flushed)",
                  "bound": "hbm", "achieved": cat_gbs, "peak": hbm, "unit": "GB/s",
-                 "frac": cat_gbs / hbm, "traffic": cat_n * 1.736113e9 / 208e6,
-                 "traffic_source": "profiles/validate_b_training_trace_208M.md (ncu DRAM bytes "
-                                   "of 208M records), scaled by records",
+                 "frac": cat_gbs / hbm, "traffic": cat_n * TRAFFIC_260M / 260e6,
+                 "traffic_source": "profiles/validate_b_distinct_traces_260M.md (ncu DRAM bytes "
+                                   "of the 260M-record launch), scaled by records",
                  "accesses_per_s": cat_n / (cat_ms * 1e-3), "launch_us": 1e3 * cat_ms},
                 {"kernel": "k_validate_b, one launch over all 200 distinct traces (260M "
                            "records, 2.1 GB, union of their speculated sets, L2 flushed)",
                  "bound": "hbm", "achieved": all_gbs, "peak": hbm, "unit": "GB/s",
-                 "frac": all_gbs / hbm, "traffic": None,
+                 "frac": all_gbs / hbm, "traffic": TRAFFIC_260M * all_n / 260e6,
+                 "traffic_source": "profiles/validate_b_distinct_traces_260M.md (ncu DRAM bytes "
+                                   "of this launch)",
                  "accesses_per_s": all_n / (all_ms * 1e-3), "launch_us": 1e3 * all_ms},
                 {"kernel": "k_copy_main, CoW live -> staging (%d buffers, %.2f GB)"
                            % (len(rows), off / 1e9),
                  "bound": "hbm", "achieved": d2d_gbs, "peak": hbm, "unit": "GB/s",
-                 "frac": d2d_gbs / hbm, "traffic": 2 * off * 0.99,
-                 "traffic_source": "profiles/copy_main_d2d_2GB.md (DRAM bytes = 0.99 x "
+                 "frac": d2d_gbs / hbm, "traffic": 2 * off * TRAFFIC_COPY_D2D_RATIO,
+                 "traffic_source": "profiles/copy_main_d2d_2GB.md (DRAM bytes = 0.988 x "
                                    "algorithmic), scaled to this launch"}],
             "rooflines_clocks": roof_clocks,
             "breakdown_ms_per_step": {k: v / args.steps for k, v in phase.items()},

@@ -129,6 +129,8 @@ def bench_validate_distinct(K, out, reps=5):
     vv = torch.empty(256, dtype=torch.uint8, device="cuda")
     st = torch.zeros(4, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush_r = torch.ones(256 << 20, dtype=torch.uint8, device="cuda")
+    acc = torch.zeros(1, dtype=torch.int64, device="cuda")
 
     def run(perm, ptr, nrec):
         phos.validate(t, perm.data_ptr(), ptr, nrec, 4, bm.data_ptr(), cnt.data_ptr(),
@@ -138,7 +140,11 @@ def bench_validate_distinct(K, out, reps=5):
         fn()
         ts = []
         for _ in range(reps):
-            flush.zero_()                            # L2 flush (2 x L2)
+            # L2 flush: a 256 MB write, then a 256 MB read of another
+            # buffer, so that no dirty lines are left for the timed launch
+            # to write back
+            flush.zero_()
+            torch.sum(flush_r.view(torch.int64), dim=(0,), out=acc[0])
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
