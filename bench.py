@@ -570,7 +570,9 @@ def run_gpu(args, rank, world):
                        "rounds": {"sync": "host waits for each kernel's validation",
                                   "nosync": "no wait per kernel, validation rule on the device",
                                   "concurrent": "no wait per kernel, copier on its own stream "
-                                                "(event ordering)"}[args.rounds],
+                                                "(event ordering)",
+                                  "deferred": "concurrent, up to 16 rounds validated per "
+                                              "launch"}[args.rounds],
                        "l2": "inputs larger than L2 (image %.1f GB, traces %.2f GB)"
                              % (dp.image_bytes / 1e9, h2d / 1e9),
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -1415,23 +1417,25 @@ def run_rounds(args, rank, world):
         torch.cuda.synchronize()
         return {"rounds": n_k, "ms_per_round": 1e3 * (time.perf_counter() - t0) / n_k}
 
-    for r in ("sync", "nosync", "concurrent"):
+    for r in ("sync", "nosync", "concurrent", "deferred"):
         session(r)
     session("device", cow=True)
     l0 = phos.launch_count()
     res = {"kernels_alone": alone()}
-    for r in ("sync", "nosync", "concurrent"):
+    for r in ("sync", "nosync", "concurrent", "deferred"):
         res["recopy_" + r] = session(r)
         res["cow_" + r] = session(r, cow=True)
     res["cow_device"] = session("device", cow=True)
-    for r in ("sync", "concurrent"):
+    for r in ("sync", "concurrent", "deferred"):
         native(r)
         res["native_recopy_" + r] = native(r)
         res["native_cow_" + r] = native(r, cow=True)
     launches = phos.launch_count() - l0
     assert res["recopy_sync"]["dirty"] == res["recopy_concurrent"]["dirty"]
+    assert res["recopy_sync"]["dirty"] == res["recopy_deferred"]["dirty"]
     assert res["native_recopy_sync"]["dirty"] == res["recopy_sync"]["dirty"]
-    best = res["native_recopy_concurrent"]
+    best = min((res["native_recopy_concurrent"], res["native_recopy_deferred"]),
+               key=lambda a: a["ms_per_round"])
     line = {"metric": METRIC, "value": 1e3 / best["ms_per_round"],
             "unit": "kernel rounds/s", "higher_is_better": True, "n_gpus": world, "steps": 1,
             "warmup": 1, "ms_per_step": best["ms_per_round"] * best["rounds"],
@@ -1466,9 +1470,11 @@ def main():
     ap.add_argument("--dma-min", type=int, default=256 << 10,
                     help="smallest host-leg piece for the DMA engines (smaller ones: SM copy "
                          "kernel)")
-    ap.add_argument("--rounds", default="concurrent", choices=["sync", "nosync", "concurrent"],
+    ap.add_argument("--rounds", default="concurrent",
+                    choices=["sync", "nosync", "concurrent", "deferred"],
                     help="nosync: protocol rounds do not wait for validation (device-side "
-                         "rule); concurrent: also the copier on its own stream")
+                         "rule); concurrent: also the copier on its own stream; deferred: "
+                         "also up to 16 rounds validated per launch")
     ap.add_argument("--server-window", type=int, default=0,
                     help="serving: host-leg MiB queued per direction (0 = two 64 MiB batches)")
     ap.add_argument("--headline-only", action="store_true",

@@ -512,6 +512,20 @@ phos_status phos_copier_window(uint64_t bytes);
  * PHOS_ENOMEM if exceeded).  Copies are all SM-issued (no DMA host legs:
  * the host does not see the pieces). */
 enum { PHOS_CKPT_DEVICE = 0x400 };
+/* OR'ed into mode or restore flags (implies PHOS_CKPT_NO_SYNC; not with
+ * PHOS_CKPT_DEVICE): after_kernel does not launch the round's validation.
+ * It queues the round, and up to 16 queued rounds are validated in one
+ * launch -- each round's trace against that round's speculated
+ * permissions, and the protocol's rule answered with that round's flags,
+ * as the launch per round would -- when the queue is full, and before
+ * anything that reads the rule's results or recycles the session's upload
+ * arena (finish, stats, logs, begin_pass, a roll-back).  Results are the
+ * no-sync mode's; a mis-speculation reaches the host up to 16 rounds later
+ * (at the latest at finish).  A round's trace must stay unchanged in device
+ * memory until it has been validated: until 16 more rounds have run, or
+ * until finish.  A table too large for two rounds' permissions and victim
+ * sets in one CTA's shared memory validates each round at once. */
+enum { PHOS_CKPT_DEFER = 0x800 };
 
 typedef struct {
     uint32_t mode;           /* PHOS_CKPT_COW (Sec. 4.2) or PHOS_CKPT_RECOPY

@@ -18,6 +18,11 @@
 // a validation result, so the host can run ahead of the device; it learns
 // of a CoW mis-speculation from the mapped word at its next call, and at
 // the latest at finish, which then copies every buffer stop-the-world.
+// With PHOS_CKPT_DEFER a no-sync session goes one step further: after_kernel
+// only queues the round (trace, perm slot, rule-flag slot, round number),
+// and up to kMaxRounds queued rounds are validated in one launch
+// (validate_rounds) -- when the queue is full, and before anything that
+// reads the rule's results or recycles the upload arena.
 #include <limits.h>
 #include <math.h>
 #include <string.h>
@@ -165,6 +170,11 @@ struct Session {
     uint32_t *d_vic = nullptr;      // victim | victim_st
     uint8_t *d_dirty = nullptr;     // u8[n]
     int64_t *h_flag = nullptr, *d_flag = nullptr;
+    // deferred validation (PHOS_CKPT_DEFER): rounds queued for one launch
+    uint32_t defer_k = 0;            // rounds per launch, 0 = validate at once
+    uint32_t defer_rule = 0;         // ProtoRule kind of the queued rounds
+    std::vector<RoundSeg> pend;
+    void *d_rscratch = nullptr;
     // concurrent sessions: the copier's own stream, a clone of the table
     // (its own copy-engine scratch), one event per copier batch, kept until
     // that batch has completed (batches complete in order on the copier
@@ -221,6 +231,27 @@ struct Session {
         return reserve_list(65536);
     }
 
+    // Deferred validation (after init_nosync); a table too large for even
+    // two rounds per launch keeps validating at once.
+    phos_status init_defer() {
+        defer_k = rounds_cap(n, t->device);
+        if (!defer_k) return PHOS_OK;
+        const size_t b = rounds_scratch_bytes(n, kMaxRounds);
+        PHOS_CUDA(cudaMalloc(&d_rscratch, b));
+        PHOS_CUDA(cudaMemset(d_rscratch, 0, b));
+        pend.reserve(kMaxRounds);
+        return PHOS_OK;
+    }
+
+    // Validate the queued rounds (one launch, on the caller's stream).
+    phos_status flush_pending() {
+        if (pend.empty()) return PHOS_OK;
+        phos_status r = validate_rounds(t, pend.data(), (uint32_t)pend.size(), w, defer_rule,
+                                        d_dirty, d_acc, d_flag, d_status, d_rscratch, s);
+        pend.clear();
+        return r;
+    }
+
     phos_status init_concurrent() {
         phos_status r = init_nosync();
         if (r) return r;
@@ -234,8 +265,10 @@ struct Session {
         return PHOS_OK;
     }
 
-    // Both streams (the upload and list arenas are shared by them).
+    // Both streams (the upload and list arenas are shared by them); queued
+    // rounds are validated first (their slots live in the upload arena).
     cudaError_t sync_streams() {
+        if (!pend.empty() && flush_pending() != PHOS_OK) return cudaErrorLaunchFailure;
         cudaError_t e = cudaStreamSynchronize(s);
         if (e == cudaSuccess && cs) e = cudaStreamSynchronize(cs);
         return e;
@@ -332,6 +365,7 @@ struct Session {
         if (d_acc) cudaFree(d_acc);
         if (d_vic) cudaFree(d_vic);
         if (d_dirty) cudaFree(d_dirty);
+        if (d_rscratch) cudaFree(d_rscratch);
         if (h_flag) cudaFreeHost(h_flag);
         if (h_list) cudaFreeHost(h_list);
         if (d_list) cudaFree(d_list);
@@ -480,6 +514,18 @@ struct Session {
     // rule: 0 recopy (dirty marks), 1 CoW (store victims not safe), 2
     // restore (victims of any access not restored).
     phos_status validate_nosync(const uint64_t *d_trace, uint64_t n_rec, int rule) {
+        if (defer_k && !perm_dev) {
+            if (n_rec && !d_trace) return fail(PHOS_EINVAL, "validate: NULL trace");
+            if (n_rec && ((uintptr_t)d_trace & 15))
+                return fail(PHOS_EINVAL, "validate: trace must be 16-byte aligned");
+            defer_rule = rule == 0 ? 1u : (rule == 1 ? 2u : 3u);
+            // an empty trace has no victim: the rule would change nothing
+            if (n_rec)
+                pend.push_back(RoundSeg{d_trace, n_rec, d_up + slot, d_up + slot + n,
+                                        (int64_t)round - 1});
+            validated += n_rec;
+            return pend.size() >= defer_k ? flush_pending() : PHOS_OK;
+        }
         // growth synchronises: this round's slot is uploaded by then and
         // later uploads into its device copy are stream-ordered after the
         // validation below
@@ -645,14 +691,16 @@ extern "C" phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_de
                                        phos_stream_t stream, phos_ckpt_t **out) {
     if (!t || !d || !out) return fail(PHOS_EINVAL, "ckpt_begin: NULL argument");
     *out = nullptr;
-    const uint32_t mode =
-        d->mode & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT | PHOS_CKPT_DEVICE);
+    const uint32_t mode = d->mode & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT |
+                                                PHOS_CKPT_DEVICE | PHOS_CKPT_DEFER);
     if (mode != PHOS_CKPT_COW && mode != PHOS_CKPT_RECOPY)
         return fail(PHOS_EINVAL, "ckpt_begin: mode %u", d->mode);
     if ((d->mode & PHOS_CKPT_DEVICE) &&
         (mode != PHOS_CKPT_COW || (d->mode & PHOS_CKPT_CONCURRENT)))
         return fail(PHOS_EINVAL, "ckpt_begin: PHOS_CKPT_DEVICE is for CoW sessions, without "
                                  "PHOS_CKPT_CONCURRENT");
+    if ((d->mode & PHOS_CKPT_DEFER) && (d->mode & PHOS_CKPT_DEVICE))
+        return fail(PHOS_EINVAL, "ckpt_begin: PHOS_CKPT_DEFER goes without PHOS_CKPT_DEVICE");
     if (d->access_bytes == 0 || d->chunk == 0 || d->chunk % 256)
         return fail(PHOS_EINVAL, "ckpt_begin: access_bytes >= 1, chunk a multiple of 256");
     if (!d->image || d->image_bytes < t->image_bytes)
@@ -668,8 +716,12 @@ extern "C" phos_status phos_ckpt_begin(const phos_table_t *t, const phos_ckpt_de
         delete c;
         return r;
     }
-    if ((d->mode & (PHOS_CKPT_NO_SYNC | PHOS_CKPT_DEVICE)) && !c->ss.nosync &&
+    if ((d->mode & (PHOS_CKPT_NO_SYNC | PHOS_CKPT_DEVICE | PHOS_CKPT_DEFER)) && !c->ss.nosync &&
         (r = c->ss.init_nosync())) {
+        delete c;
+        return r;
+    }
+    if ((d->mode & PHOS_CKPT_DEFER) && (r = c->ss.init_defer())) {
         delete c;
         return r;
     }
@@ -1125,16 +1177,21 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
     if (!d->image || d->image_bytes < t->image_bytes)
         return fail(PHOS_EINVAL, "restore_begin: image smaller than %llu bytes",
                     (unsigned long long)t->image_bytes);
-    if (d->flags & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT | PHOS_CKPT_DEVICE))
+    if (d->flags & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT | PHOS_CKPT_DEVICE |
+                               PHOS_CKPT_DEFER))
         return fail(PHOS_EINVAL, "restore_begin: flags %#x", d->flags);
+    if ((d->flags & PHOS_CKPT_DEFER) && (d->flags & PHOS_CKPT_DEVICE))
+        return fail(PHOS_EINVAL, "restore_begin: PHOS_CKPT_DEFER goes without PHOS_CKPT_DEVICE");
     if ((d->flags & PHOS_CKPT_DEVICE) && ((d->flags & PHOS_CKPT_CONCURRENT) || d->d_manifest))
         return fail(PHOS_EINVAL, "restore_begin: PHOS_CKPT_DEVICE goes without "
                                  "PHOS_CKPT_CONCURRENT and without a manifest");
     phos_restore *r = new phos_restore();
     phos_status e = r->ss.init(t, static_cast<cudaStream_t>(stream), d->access_bytes, d->chunk);
     if (!e && (d->flags & PHOS_CKPT_CONCURRENT)) e = r->ss.init_concurrent();
-    if (!e && (d->flags & (PHOS_CKPT_NO_SYNC | PHOS_CKPT_DEVICE)) && !r->ss.nosync)
+    if (!e && (d->flags & (PHOS_CKPT_NO_SYNC | PHOS_CKPT_DEVICE | PHOS_CKPT_DEFER)) &&
+        !r->ss.nosync)
         e = r->ss.init_nosync();
+    if (!e && (d->flags & PHOS_CKPT_DEFER)) e = r->ss.init_defer();
     if (!e && (d->flags & PHOS_CKPT_DEVICE)) {
         r->dr = new DevRounds();
         e = r->dr->init(t, 1, d->chunk, 0, d->d_present != nullptr, r->ss.s);

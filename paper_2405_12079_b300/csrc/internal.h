@@ -77,6 +77,27 @@ phos_status validate_impl(const phos_table_t *t, const uint8_t *d_perm, const ui
                           uint64_t *d_idx, uint64_t idx_cap, uint32_t *d_status,
                           phos_stream_t stream, const ProtoRule *rule, bool *rule_fused);
 
+// Several rounds' validation in one launch (deferred no-sync sessions):
+// round i's trace checked against its own perm, its rule answered with its
+// own flags (rule kind as in ProtoRule; dirty, acc and h_flag as there).
+constexpr uint32_t kMaxRounds = 16;
+struct RoundSeg {
+    const uint64_t *trace;
+    uint64_t n_rec;
+    const uint8_t *perm;
+    const uint8_t *flags;
+    int64_t round;
+};
+// Rounds one launch can take for a table of n buffers (0: none fit).
+uint32_t rounds_cap(uint32_t n, int device);
+// Bytes of zeroed device scratch a launch of up to k rounds needs (the
+// kernel leaves it zeroed).
+size_t rounds_scratch_bytes(uint32_t n, uint32_t k);
+phos_status validate_rounds(const phos_table_t *t, const RoundSeg *seg, uint32_t k,
+                            uint32_t access_bytes, uint32_t rule, uint8_t *d_dirty,
+                            uint64_t *d_acc, int64_t *d_flag, uint32_t *d_status,
+                            void *d_scratch, cudaStream_t s);
+
 }  // namespace phos
 
 struct phos_table;

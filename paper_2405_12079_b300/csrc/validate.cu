@@ -675,13 +675,6 @@ static uint32_t g_val_variant = 0;  // 0 auto, 1 TMA ring, 2 batched leaders
 static uint32_t g_val_wait_limit = kWaitLimit;
 static uint32_t g_val_ctas = 0;     // 0 auto (one per SM), else the grid size
 
-// Words per warp batch, W in {32, 16, 8}: the one that minimises the
-// busiest warp's work, words x (W + 6) / W -- each batch costs its leader
-// searches on top of its words, which makes an 8-word batch ~1.45x and a
-// 16-word batch ~1.15x as dear per record as a 32-word one (measured:
-// 260M records took 0.60 ms with 8-word batches, 0.41 ms with 32).  Small
-// traces still spread over every warp; large ones keep W = 32 even where a
-// smaller W would shave a partial batch off the tail.
 // CTAs of a batched launch: one per 8 batches up to the SM count.  A CTA's
 // prologue (table and perms into shared memory) and its part in the
 // last-CTA reduction cost the same whether it has one busy warp or 32, and
@@ -691,6 +684,13 @@ static uint64_t batched_grid(uint64_t units, uint64_t ctas) {
     return std::max<uint64_t>(1, std::min<uint64_t>(ctas, (units + 7) / 8));
 }
 
+// Words per warp batch, W in {32, 16, 8}: the one that minimises the
+// busiest warp's work, words x (W + 6) / W -- each batch costs its leader
+// searches on top of its words, which makes an 8-word batch ~1.45x and a
+// 16-word batch ~1.15x as dear per record as a 32-word one (measured:
+// 260M records took 0.60 ms with 8-word batches, 0.41 ms with 32).  Small
+// traces still spread over every warp; large ones keep W = 32 even where a
+// smaller W would shave a partial batch off the tail.
 static uint32_t words_per_batch(uint64_t n_rec, uint64_t ctas) {
     const uint64_t warps = ctas * (kValThreads / 32);
     uint32_t best = 32;

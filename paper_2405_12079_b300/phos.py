@@ -105,6 +105,7 @@ CKPT_COW, CKPT_RECOPY = 1, 2
 CKPT_NO_SYNC = 0x100
 CKPT_CONCURRENT = 0x200
 CKPT_DEVICE = 0x400
+CKPT_DEFER = 0x800
 
 
 REQ_CHECKPOINT, REQ_RESTORE = 1, 2

@@ -88,11 +88,14 @@ class DeviceProcess:
     @staticmethod
     def _flags(rounds):
         """rounds: "sync" (wait for each validation), "nosync" (rule on the
-        device), "concurrent" (nosync, copier on its own stream) or "device"
+        device), "concurrent" (nosync, copier on its own stream), "deferred"
+        (concurrent, up to 16 rounds validated per launch) or "device"
         (every round's decisions on the device, perms from device
         speculation)."""
         return {"sync": 0, "nosync": phos.CKPT_NO_SYNC,
-                "concurrent": phos.CKPT_CONCURRENT, "device": phos.CKPT_DEVICE}[rounds]
+                "concurrent": phos.CKPT_CONCURRENT,
+                "deferred": phos.CKPT_CONCURRENT | phos.CKPT_DEFER,
+                "device": phos.CKPT_DEVICE}[rounds]
 
     def device_perms(self):
         """Every kernel's speculated permissions, computed on the device in

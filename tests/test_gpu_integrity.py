@@ -40,7 +40,7 @@ def manifest(dp, img):
     return d
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "deferred"])
 def test_verified_restore(rounds):
     lay, arena, ks, dp, proc = world(wl.SEED0 + 31)
     image = P.stw_checkpoint(proc)
@@ -53,7 +53,8 @@ def test_verified_restore(rounds):
     # intact image: verified restore == the oracle's restore + replay
     arena.fill_(0xA5)
     cur = P.Process(dp.va0, lay.off, lay.size, np.full(lay.arena_bytes, 0xA5, np.uint8), proc.seed)
-    exp = P.concurrent_restore(cur, image, ks, chunk, quota, copier_stream=rounds == "concurrent")
+    exp = P.concurrent_restore(cur, image, ks, chunk, quota,
+                               copier_stream=rounds in ("concurrent", "deferred"))
     got = dp.run_restore(img, quota, chunk, rounds=rounds, d_manifest=d_man)
     torch.cuda.synchronize()
     assert got["stats"]["corrupt_buf"] == -1 and got["stats"]["misspec_round"] == -1

@@ -97,14 +97,15 @@ def check_ckpt(w, mode, quota, chunk, staging_bytes=0, rounds="sync"):
     return got, exp
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "device"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "deferred", "device"])
 @pytest.mark.parametrize("mode", ["cow", "recopy"])
 def test_training_image_scaled(mode, rounds):
     """Training-process shape at 1/500 scale (1,000 buffers, ~80 MB,
     200 kernels); quota = image/100, chunk 64 KiB, staging 4 MB.  The
-    no-sync rounds (rule on the device, no wait per kernel) and the
-    concurrent copier (its own stream, event ordering) give exactly the
-    lockstep results."""
+    no-sync rounds (rule on the device, no wait per kernel), the
+    concurrent copier (its own stream, event ordering) and deferred
+    validation (up to 16 rounds per launch) give exactly the lockstep
+    results."""
     if mode == "recopy" and rounds == "device":
         pytest.skip("device-decided rounds are for CoW and restore sessions")
     w, cfg = training_world(wl.SEED0 + 2, 0.002, 200)
@@ -127,7 +128,7 @@ def test_stray_stores_fault_injection(mode):
         assert exp.misspec is not None
 
 
-@pytest.mark.parametrize("rounds", ["nosync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["nosync", "concurrent", "deferred"])
 def test_stray_stores_recopy_nosync(rounds):
     """Recopy without a wait per kernel: the store victims reach the dirty
     set through the device-side rule; everything equals the oracle."""
@@ -137,7 +138,7 @@ def test_stray_stores_recopy_nosync(rounds):
     assert got["stats"]["violations"] > 0
 
 
-@pytest.mark.parametrize("rounds", ["nosync", "concurrent", "device"])
+@pytest.mark.parametrize("rounds", ["nosync", "concurrent", "deferred", "device"])
 def test_stray_stores_cow_nosync_falls_back_at_finish(rounds):
     """CoW without a wait per kernel on the mis-speculating workload: the
     device records the same first mis-speculated round as the oracle; the
@@ -204,7 +205,7 @@ def check_restore(w, quota, chunk, rounds="sync"):
     w.arena.fill_(0xA5)
     cur = w.oracle_proc(np.full(w.lay.arena_bytes, 0xA5, np.uint8))
     exp = P.concurrent_restore(cur, image, w.kernels, chunk, quota,
-                               copier_stream=rounds == "concurrent")
+                               copier_stream=rounds in ("concurrent", "deferred"))
     present = torch.zeros(4 * ((w.lay.n + 31) // 32), dtype=torch.uint8, device="cuda")
     got = w.dp.run_restore(img, quota, chunk, present, rounds=rounds)
     torch.cuda.synchronize()
@@ -225,7 +226,7 @@ def check_restore(w, quota, chunk, rounds="sync"):
 
 
 @pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "concurrent-window",
-                                    "device"])
+                                    "deferred", "device"])
 def test_large_restore_scaled(rounds):
     """Large-restore shape at small scale: 10,000 buffers, layer-local
     read/write sets, background bulk restore plus on-demand copies.  With a
@@ -246,7 +247,7 @@ def test_large_restore_scaled(rounds):
     assert len(exp.ondemand) > 0
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "device"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "deferred", "device"])
 def test_restore_stray_load_rolls_back(rounds):
     cfg = wl.training(scale=0.0005, seed=wl.SEED0 + 22, n_kernels=40)
 
@@ -260,7 +261,7 @@ def test_restore_stray_load_rolls_back(rounds):
 @pytest.mark.parametrize("div,n_kernels,stray,max_passes,stop", [
     (100, 200, 0.0, 6, 0), (30, 200, 0.0, 6, 0), (30, 200, 0.0, 1, 0),
     (20, 120, 0.3, 6, 1 << 20)])
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "deferred"])
 def test_iterative_recopy(div, n_kernels, stray, max_passes, stop, rounds):
     """Iterative concurrent recopy (Sec. 4.3): the passes (round, buffers,
     bytes), the copier pieces across passes, the final dirty set, the image
@@ -289,7 +290,7 @@ def test_iterative_recopy(div, n_kernels, stray, max_passes, stop, rounds):
     assert w.live_equal(proc)
 
 
-@pytest.mark.parametrize("rounds", ["sync", "concurrent"])
+@pytest.mark.parametrize("rounds", ["sync", "concurrent", "deferred"])
 @pytest.mark.parametrize("mode", ["cow", "recopy"])
 def test_native_driver_equals_oracle(mode, rounds):
     """The library's native round driver gives the oracle's results too."""
