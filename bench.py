@@ -840,7 +840,7 @@ def serving_line(args, world, window=None):
     torch.cuda.synchronize()
 
     def run(slots):
-        srv = phos.Server(slots, staging.data_ptr(), stg_b, chunk=4 << 20, dma_min=1 << 20,
+        srv = phos.Server(slots, staging.data_ptr(), stg_b, chunk=4 << 20, dma_min=args.dma_min,
                           window=args.server_window << 20)
         tickets = [None] * len(tables)
         errors = []
