@@ -960,7 +960,7 @@ def restore_line(args, world):
 
     def stw():
         """Stop-the-world: restore every buffer (same host-leg path as the
-        concurrent session: DMA engines for >= 1 MiB pieces), then replay."""
+        concurrent session: DMA engines for pieces from --dma-min), then replay."""
         phos.harness_fill(arena.data_ptr(), lay.arena_bytes, 9, s)     # lose the state
         torch.cuda.synchronize()
         a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))

@@ -523,8 +523,10 @@ enum { PHOS_CKPT_DEVICE = 0x400 };
  * no-sync mode's; a mis-speculation reaches the host up to 16 rounds later
  * (at the latest at finish).  A round's trace must stay unchanged in device
  * memory until it has been validated: until 16 more rounds have run, or
- * until finish.  A table too large for two rounds' permissions and victim
- * sets in one CTA's shared memory validates each round at once. */
+ * until finish.  A round whose trace is longer than 2^24 records, and every
+ * round of a table too large for two rounds' permissions and victim sets
+ * in one CTA's shared memory, is validated at once (after the queued
+ * rounds). */
 enum { PHOS_CKPT_DEFER = 0x800 };
 
 typedef struct {

@@ -170,7 +170,10 @@ struct Session {
     uint32_t *d_vic = nullptr;      // victim | victim_st
     uint8_t *d_dirty = nullptr;     // u8[n]
     int64_t *h_flag = nullptr, *d_flag = nullptr;
-    // deferred validation (PHOS_CKPT_DEFER): rounds queued for one launch
+    // deferred validation (PHOS_CKPT_DEFER): rounds queued for one launch;
+    // traces longer than kDeferMaxRec records are validated at once by the
+    // streaming kernel, which is the faster one at that length
+    static constexpr uint64_t kDeferMaxRec = 1ull << 24;
     uint32_t defer_k = 0;            // rounds per launch, 0 = validate at once
     uint32_t defer_rule = 0;         // ProtoRule kind of the queued rounds
     std::vector<RoundSeg> pend;
@@ -514,7 +517,12 @@ struct Session {
     // rule: 0 recopy (dirty marks), 1 CoW (store victims not safe), 2
     // restore (victims of any access not restored).
     phos_status validate_nosync(const uint64_t *d_trace, uint64_t n_rec, int rule) {
-        if (defer_k && !perm_dev) {
+        // a long trace goes to the streaming kernel at once (after the
+        // queued rounds, so the rule still sees rounds in order)
+        if (defer_k && !perm_dev && n_rec > kDeferMaxRec) {
+            phos_status rf = flush_pending();
+            if (rf) return rf;
+        } else if (defer_k && !perm_dev) {
             if (n_rec && !d_trace) return fail(PHOS_EINVAL, "validate: NULL trace");
             if (n_rec && ((uintptr_t)d_trace & 15))
                 return fail(PHOS_EINVAL, "validate: trace must be 16-byte aligned");

@@ -582,7 +582,7 @@ class Plan:
 class Server:
     """Continuous-batching request loop (phos_server_*)."""
 
-    def __init__(self, max_slots, d_staging, staging_bytes, chunk=4 << 20, dma_min=1 << 20,
+    def __init__(self, max_slots, d_staging, staging_bytes, chunk=4 << 20, dma_min=256 << 10,
                  app_priority=False, window=0):
         d = ServerDesc(max_slots, SERVER_APP_PRIORITY if app_priority else 0, d_staging,
                        staging_bytes, chunk, dma_min, window)
