@@ -43,3 +43,29 @@ def test_host_only_calls_without_gpu():
     assert L.phos_table_create(bufs.ctypes.data, 2, ctypes.byref(h)) == phos.PHOS_EINVAL
     assert b"unsorted" in L.phos_last_error()
     assert L.phos_copy_config(1000, 0) == phos.PHOS_EINVAL
+
+
+def header_enums():
+    """NAME -> value of every enumerator in the public headers."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+            for m in re.finditer(r"\b(PHOS_[A-Z0-9_]+)\s*=\s*(0x[0-9a-fA-F]+|\d+)", body):
+                out[m.group(1)] = int(m.group(2), 0)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """Every constant the binding defines under a header enumerator's name
+    (with or without the PHOS_ prefix) has the header's value."""
+    enums = header_enums()
+    assert len(enums) >= 25
+    checked = 0
+    for name, value in enums.items():
+        for attr in (name, name[len("PHOS_"):]):
+            if hasattr(phos, attr):
+                assert getattr(phos, attr) == value, (attr, getattr(phos, attr), value)
+                checked += 1
+    assert checked >= 20
+    assert phos.CKPT_DEFER == enums["PHOS_CKPT_DEFER"]
