@@ -174,6 +174,9 @@ struct phos_table {
 namespace phos {
 // device SM count (cached per device)
 int sm_count(int device);
+// Opt kernel fn in to 227 KB of dynamic shared memory on the current device
+// (once per kernel and device; thread-safe).
+phos_status smem_optin_once(const void *fn);
 // Resolve an image pointer to a device-accessible address (pinned host ->
 // mapped device pointer; device -> itself).  EINVAL for pageable memory.
 phos_status device_view(const void *p, void **out);

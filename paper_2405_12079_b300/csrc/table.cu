@@ -6,6 +6,9 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "internal.h"
 
@@ -55,6 +58,18 @@ phos_status Scratch::reserve(size_t need) {
 
 Scratch::~Scratch() {
     if (ptr) cudaFree(ptr);
+}
+
+phos_status smem_optin_once(const void *fn) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    PHOS_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if (done.count({fn, dev})) return PHOS_OK;
+    PHOS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    done.insert({fn, dev});
+    return PHOS_OK;
 }
 
 int sm_count(int device) {

@@ -713,13 +713,16 @@ using namespace phos;
 
 namespace {
 
+// always_attr: set the shared-memory opt-in on every call (the allocation-
+// free entry point keeps no host-side state either).
 template <bool T, bool D>
 phos_status launch_b(uint64_t G, size_t smem, cudaStream_t s, const ValParams &p, bool always_attr) {
-    static bool attr_done = false;
-    if (always_attr || !attr_done) {
+    if (always_attr) {
         PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_b<T, D>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-        attr_done = true;
+    } else {
+        phos_status r = smem_optin_once((const void *)k_validate_b<T, D>);
+        if (r) return r;
     }
     k_validate_b<T, D><<<(unsigned)G, kValThreads, smem, s>>>(p);
     return PHOS_OK;
@@ -816,15 +819,7 @@ phos_status phos::validate_impl(const phos_table_t *t, const uint8_t *d_perm,
         p.rule = *rule;
         if (rule_fused) *rule_fused = true;
     }
-    static bool attr_done[2] = {false, false};
-    auto attr = [&](const void *fn, int slot) -> phos_status {
-        if (!attr_done[slot]) {
-            PHOS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           227 * 1024));
-            attr_done[slot] = true;
-        }
-        return PHOS_OK;
-    };
+    auto attr = [&](const void *fn, int) -> phos_status { return smem_optin_once(fn); };
     phos_status r;
     if (variant == 1) {
         ValPlan pl = plan_validate(t->n, T->device);

@@ -249,22 +249,13 @@ phos_status validate_rounds(const phos_table_t *t, const RoundSeg *seg, uint32_t
     const uint64_t warps_per_cta = kRoundThreads / 32;
     const uint64_t G = std::max<uint64_t>(
         1, std::min<uint64_t>(2ull * sm_count(t->device), (b + warps_per_cta - 1) / warps_per_cta));
-    static bool attr_done[2] = {false, false};
     if (table) {
-        if (!attr_done[0]) {
-            PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_rounds<true>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           227 * 1024));
-            attr_done[0] = true;
-        }
+        phos_status r = smem_optin_once((const void *)k_validate_rounds<true>);
+        if (r) return r;
         k_validate_rounds<true><<<(unsigned)G, kRoundThreads, smem, s>>>(p);
     } else {
-        if (!attr_done[1]) {
-            PHOS_CUDA(cudaFuncSetAttribute((const void *)k_validate_rounds<false>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           227 * 1024));
-            attr_done[1] = true;
-        }
+        phos_status r = smem_optin_once((const void *)k_validate_rounds<false>);
+        if (r) return r;
         k_validate_rounds<false><<<(unsigned)G, kRoundThreads, smem, s>>>(p);
     }
     count_launch();
