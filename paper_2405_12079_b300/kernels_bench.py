@@ -203,6 +203,44 @@ def bench_emit(K, out):
         emit_ms=ms_idx - ms_plain)
 
 
+def bench_validate_rounds(out, K=64, n_rec=65536):
+    """Recopy sessions of K kernel rounds with n_rec-record traces over the
+    1,000-buffer training layout (1/20 scale, the copier held to 256 bytes
+    per round): one validation launch per round against up to 16 rounds per
+    launch (deferred validation).  Times the rounds only (K is a multiple
+    of 16, so every queued round is validated inside the timed region)."""
+    import time
+    from . import runner
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(scale=0.05, n_kernels=K)
+    rng, lay = cfg["rng"], cfg["layout"]
+    arena = torch.empty(lay.arena_bytes, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(arena.data_ptr(), lay.arena_bytes, cfg["seed"], s)
+    kernels = wl.make_training_kernels(rng, lay, arena.data_ptr(), K, n_rec, 0.001)
+    dp = runner.DeviceProcess(lay, arena, cfg["seed"], kernels)
+    image = torch.empty(dp.image_bytes, dtype=torch.uint8).pin_memory()
+    ks = dp.native_kernels()
+
+    def session(flags):
+        c = phos.Checkpoint(dp.table, phos.CKPT_RECOPY | flags, image.data_ptr(), image.numel(),
+                            4 << 20, 4, None, 0, s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = phos.harness_drive_ckpt(c, dp.table, dp.seed, 256, ks, s)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        dirty = c.stats()["dirty"]
+        c.finish()
+        c.close()
+        return 1e3 * (t1 - t0) / k, dirty
+    for name, flags in (("concurrent", phos.CKPT_CONCURRENT),
+                        ("deferred", phos.CKPT_CONCURRENT | phos.CKPT_DEFER)):
+        session(flags)
+        best, dirty = min(session(flags) for _ in range(3))
+        out["rounds_" + name] = dict(rounds=K, records_per_round=n_rec, ms_per_round=best,
+                                    dirty=dirty)
+
+
 def bench_copy_misaligned(gb, out):
     """Device -> device copies of G GB in 4 MB regions whose source is
     offset from the destination's alignment by 0, 1, 2, 4, 8 or 12 bytes."""
@@ -327,7 +365,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", default="all",
                     choices=["validate", "validate_distinct", "emit", "copy", "copy_misaligned",
-                             "speculate", "all"])
+                             "validate_rounds", "speculate", "all"])
     ap.add_argument("--traces", type=int, default=160)
     ap.add_argument("--copy-gb", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0, help="validate kernel variant (0 = both)")
@@ -341,6 +379,8 @@ def main():
         bench_emit(a.traces, out)
     if a.kernel == "copy_misaligned":
         bench_copy_misaligned(a.copy_gb, out)
+    if a.kernel == "validate_rounds":
+        bench_validate_rounds(out)
     if a.kernel in ("copy", "all"):
         bench_copy(a.copy_gb, out)
     if a.kernel in ("speculate", "all"):
