@@ -3,9 +3,10 @@
 // (Sec. 6).  The state machines run on the host (buffer states, the CoW
 // shadow map, the dirty set, the present set); every byte moves through
 // the copy engine and every trace through the validator, on the caller's
-// stream.  Copy lists are staged in a pinned host arena and uploaded with
-// one asynchronous copy per batch; the arena is recycled at the stream
-// synchronisations that after_kernel performs anyway to read the victims.
+// stream.  Copy lists and each round's perm and rule-flag slot are staged
+// in pinned host arenas and reach the device as kernel parameters
+// (push_small: no copy-engine upload to queue behind the copier's DMA
+// copies); the arenas are recycled at stream synchronisations.
 //
 // No-sync checkpoint sessions (PHOS_CKPT_NO_SYNC) take that round trip out:
 // after_kernel enqueues the validation, whose last CTA (or, after the ring
