@@ -347,6 +347,9 @@ def validate_wait_limit(probes=1 << 24):
     return check(lib().phos_validate_wait_limit(probes), "validate_wait_limit")
 
 
+HOST_COPY_DEFAULT = 256 << 10       # the library's default DMA threshold
+
+
 def host_copy_config(dma_min_bytes=0):
     return check(lib().phos_host_copy_config(dma_min_bytes), "host_copy_config")
 

@@ -20,7 +20,7 @@ def host_legs(request):
     with pieces of >= 16 KiB on the DMA engines; results must not change."""
     phos.host_copy_config(request.param)
     yield request.param
-    phos.host_copy_config(0)
+    phos.host_copy_config(phos.HOST_COPY_DEFAULT)
 
 
 def a256(x):

@@ -80,7 +80,7 @@ def arena_mismatches(mem, arena):
 def dma_host_legs():
     phos.host_copy_config(256 << 10)
     yield
-    phos.host_copy_config(0)
+    phos.host_copy_config(phos.HOST_COPY_DEFAULT)
 
 
 def test_training_image_full_size(dma_host_legs):
