@@ -60,9 +60,10 @@ static size_t rounds_fixed_smem() {
     return sizeof(Lead) * kRoundW * nw + 4ull * kRoundW * nw + 128;
 }
 
+// Each round's permissions sit at a 16-byte aligned stride in shared memory.
 static size_t rounds_smem(uint32_t n, uint32_t k, bool table) {
     const uint32_t nvw = std::max((n + 31) / 32, 1u);
-    return rounds_fixed_smem() + (table ? 16ull * n : 0) + align_up((uint64_t)k * n, 16) +
+    return rounds_fixed_smem() + (table ? 16ull * n : 0) + (uint64_t)k * align_up(n, 16) +
            8ull * k * nvw;
 }
 
@@ -102,11 +103,24 @@ __global__ void __launch_bounds__(kRoundThreads, 2)
         L.lim = tl;
         cur += 16ull * n;
     }
-    uint8_t *perms = cur;                                          // [K][n]
-    cur += ((uint64_t)K * n + 15) & ~15ull;
+    const uint32_t np = (n + 15) & ~15u;                         // per-round stride
+    uint8_t *perms = cur;                                          // [K][np]
+    cur += (uint64_t)K * np;
     uint32_t *sv = reinterpret_cast<uint32_t *>(cur);              // [K][2][nvw]
-    for (uint32_t s = 0; s < K; ++s)
-        for (uint32_t i = tid; i < n; i += blockDim.x) perms[(size_t)s * n + i] = p.perm[s][i];
+    for (uint32_t s = 0; s < K; ++s) {
+        // 16-byte copies where the round's slot allows (upload slots are
+        // 256-byte aligned), bytes for the rest
+        const uint8_t *src = p.perm[s];
+        uint8_t *dst = perms + (size_t)s * np;
+        uint32_t done = 0;
+        if (((uintptr_t)src & 15) == 0) {
+            const uint32_t nv = n / 16;
+            for (uint32_t i = tid; i < nv; i += blockDim.x)
+                reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(src)[i];
+            done = nv * 16;
+        }
+        for (uint32_t i = done + tid; i < n; i += blockDim.x) dst[i] = src[i];
+    }
     for (uint32_t i = tid; i < 2 * K * nvw; i += blockDim.x) sv[i] = 0;
     if (tid == 0) red[0] = 0;
     if (tid <= kMaxRounds) fw[tid] = 0;
@@ -122,16 +136,19 @@ __global__ void __launch_bounds__(kRoundThreads, 2)
         const uint64_t r0 = (b - p.bstart[s]) * kRoundBatch;
         const uint64_t nb = min(kRoundBatch, p.n_rec[s] - r0);
         const uint64_t *recs = p.trace[s] + r0;
-        L.perm = perms + (size_t)s * n;
+        L.perm = perms + (size_t)s * np;
         uint32_t *svr = sv + (size_t)s * 2 * nvw;
         if (lane < kRoundW)
             mine[lane] = make_lead(
                 L, lane * 32 < nb ? L.lane_search(recs[lane * 32] & PHOS_REC_ADDR_MASK) : -1,
                 kSmemTable);
         __syncwarp();
+        // a full batch two words per step (one 16-byte load per lane:
+        // traces are 16-byte aligned and batches start at 256-record
+        // boundaries), a partial one word by word
         if (nb == kRoundBatch)
-            batch_words<kSmemTable, true>(L, recs, nb, kRoundW, lane, mine, words + kRoundW * warp,
-                                          svr, svr + nvw, acc);
+            batch_pairs<kSmemTable>(L, recs, kRoundW, lane, mine, words + kRoundW * warp, svr,
+                                    svr + nvw, acc);
         else
             batch_words<kSmemTable, false>(L, recs, nb, kRoundW, lane, mine,
                                            words + kRoundW * warp, svr, svr + nvw, acc);

@@ -328,3 +328,53 @@ def test_device_rounds_cow_staging_pressure(budget):
         assert all(e[2] == "D" for e in exp.cow_log)
     else:
         assert {e[2] for e in exp.cow_log} == {"S", "D"}
+
+
+def test_sessions_on_two_threads_and_streams():
+    """Two processes checkpointed at once from two host threads, each on a
+    stream of its own: a concurrent deferred recopy with stray stores and a
+    concurrent CoW.  The library keeps no per-process state between them
+    (each session owns its arenas and scratch, each table its copy scratch),
+    so each result is the oracle's, as when it runs alone."""
+    import threading
+    wa, _ = training_world(wl.SEED0 + 41, 0.001, 80, stray_store_frac=0.3)
+    wb, _ = training_world(wl.SEED0 + 42, 0.001, 80)
+    chunk = 32 * 1024
+    qa, qb = a256(wa.dp.image_bytes / 60), a256(wb.dp.image_bytes / 60)
+    pa, pb = wa.oracle_proc(), wb.oracle_proc()
+    exp_a = P.recopy_checkpoint(pa, wa.kernels, chunk, qa)
+    exp_b = P.cow_checkpoint(pb, wb.kernels, 1 << 20, chunk, qb)
+    img_a = torch.zeros(wa.dp.image_bytes, dtype=torch.uint8).pin_memory()
+    img_b = torch.zeros(wb.dp.image_bytes, dtype=torch.uint8).pin_memory()
+    stg_b = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    got, errors = {}, []
+
+    def run(name, fn):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                got[name] = fn()
+                st.synchronize()
+        except Exception as e:           # reported below, in the test's thread
+            errors.append((name, e))
+    ts = [threading.Thread(target=run, args=("a", lambda: wa.dp.run_recopy(
+              img_a, qa, chunk, rounds="deferred"))),
+          threading.Thread(target=run, args=("b", lambda: wb.dp.run_cow(
+              img_b, qb, chunk, stg_b, 1 << 20, rounds="concurrent")))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    torch.cuda.synchronize()
+    ga, gb = got["a"], got["b"]
+    assert ga["dirty"].tolist() == exp_a.dirty and ga["stats"]["violations"] > 0
+    assert ga["stats"]["recopy_bytes"] == exp_a.stats["recopy_bytes"]
+    assert [tuple(int(x) for x in r) for r in ga["copier"]] == copier_rows(exp_a.copier_log)
+    assert np.array_equal(img_a.numpy(), exp_a.image)
+    assert wa.live_equal(pa)
+    assert gb["stats"]["misspec_round"] == -1 and exp_b.misspec is None
+    assert [tuple(int(x) for x in r) for r in gb["cow"]] == cow_rows(exp_b.cow_log)
+    assert [tuple(int(x) for x in r) for r in gb["copier"]] == copier_rows(exp_b.copier_log)
+    assert np.array_equal(img_b.numpy(), exp_b.image)
+    assert wb.live_equal(pb)
