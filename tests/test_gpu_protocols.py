@@ -378,3 +378,28 @@ def test_sessions_on_two_threads_and_streams():
     assert [tuple(int(x) for x in r) for r in gb["copier"]] == copier_rows(exp_b.copier_log)
     assert np.array_equal(img_b.numpy(), exp_b.image)
     assert wb.live_equal(pb)
+
+
+@pytest.mark.parametrize("mode", ["cow", "recopy"])
+def test_deferred_rounds_with_ragged_traces(mode):
+    """Deferred validation over rounds whose traces end anywhere: empty, one
+    record, inside the first batch, on and around batch and word
+    boundaries, and the full length; with stray stores (kept only where the
+    trace still holds them, so every write is validated).  The lists, dirty
+    set, image and memory equal the oracle's, as in the other modes."""
+    cfg = wl.training(scale=0.001, seed=wl.SEED0 + 43, n_kernels=60)
+    cut_rng = np.random.default_rng(4343)
+    cuts = [0, 1, 31, 32, 33, 255, 256, 257, 511, 1000, 4095]
+
+    def mk(rng, lay, va0):
+        ks = wl.make_training_kernels(rng, lay, va0, 60, cfg["n_rec"], 0.002,
+                                      0.0 if mode == "cow" else 0.3)
+        for k in ks:
+            m = int(cut_rng.choice(cuts + [len(k.trace)]))
+            k.trace = k.trace[:m]
+            k.labels = k.labels[:m]
+            k.strays = [s for s in k.strays if s[0] < m]
+        return ks
+    w = World(cfg["layout"], wl.SEED0 + 43, mk)
+    quota = a256(w.dp.image_bytes / 50)
+    check_ckpt(w, mode, quota, 32 * 1024, staging_bytes=1 << 20, rounds="deferred")

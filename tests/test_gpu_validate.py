@@ -219,3 +219,34 @@ def test_batch_assignment_around_one_batch_per_warp(ctas):
                 check(t, base, lay.size, perm, rec, 4, idx_cap=5_000)
     finally:
         phos.validate_grid(0)
+
+
+@pytest.mark.parametrize("seed", range(32))
+def test_randomized_shapes(seed):
+    """Random combinations of what the kernels branch on: table size (one
+    to three search levels, table in shared or global memory), trace length
+    (partial batches, every batch width, grid-stride or counter
+    assignment), coalesced runs mixed with independent records, reserved
+    bits, access width, permissions of every kind (W without R included),
+    grid size and index-list cap."""
+    rng = np.random.default_rng(7000 + seed)
+    n = int(rng.choice([1, 7, 33, 300, 1500, 5000]))
+    _, lay, base, t = layout_table(n, 7100 + seed, lo=64, hi=int(rng.choice([4096, 1 << 18])))
+    perm = rng.integers(0, 4, size=n).astype(np.uint8)
+    w = int(rng.choice([1, 2, 4, 8, 16]))
+    N = int(rng.choice([0, 1, 255, 257, 4097, 33_333, 150_001]))
+    reads, writes = wl.pick_sets(rng, n, 1, min(20, n))
+    m = N // 2
+    runs, _, _ = wl.trace_runs(rng, lay, VA0, reads, writes, m, stray_frac=0.02,
+                               stray_store_frac=0.4) if m else (np.zeros(0, np.uint64), 0, 0)
+    ind, _ = wl.trace_random(rng, lay, VA0, reads, N - m, w=w) if N - m else \
+        (np.zeros(0, np.uint64), 0)
+    rec = np.concatenate([np.asarray(runs, np.uint64), np.asarray(ind, np.uint64)])
+    if N and rng.random() < 0.3:               # a few malformed records
+        k = rng.choice(N, size=min(3, N), replace=False)
+        rec[k] |= np.uint64(1 << 58)
+    phos.validate_grid(int(rng.choice([0, 1, 5, 37])))
+    try:
+        check(t, base, lay.size, perm, rec, w, idx_cap=int(rng.choice([0, 1, 100, 1 << 16])))
+    finally:
+        phos.validate_grid(0)
