@@ -500,12 +500,17 @@ __global__ void __launch_bounds__(kValThreads, 1) k_validate_b(const ValParams p
         if (sv[i]) atomicOr(&p.vacc[i], sv[i]);
         if (svs[i]) atomicOr(&p.vacc[nvw + i], svs[i]);
     }
-    __threadfence();
+    // the CTA's writes are ordered before its ticket by the barrier and one
+    // fence of the thread that takes the ticket (the grid-barrier pattern);
+    // the last CTA's thread fences again before its CTA reads the others'
     __syncthreads();
-    if (tid == 0) *last = (atomicAdd(p.ticket, 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
+    if (tid == 0) {
+        __threadfence();
+        *last = (atomicAdd(p.ticket, 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
+        if (*last) __threadfence();
+    }
     __syncthreads();
     if (!*last) return;
-    __threadfence();
     sum_cta_counts(p.cta_cnt, G, tid, red);
     // the word after *last in dynamic shared memory (static shared memory
     // would cut into the 227 KB dynamic opt-in)

@@ -160,12 +160,16 @@ __global__ void __launch_bounds__(kRoundThreads, 2)
     if (tid == 0 && red[0]) atomicAdd(p.cnt, red[0]);
     for (uint32_t i = tid; i < 2 * K * nvw; i += blockDim.x)
         if (sv[i]) atomicOr(p.vacc + i, sv[i]);
-    __threadfence();
+    // ordered before the ticket by the barrier and one fence (grid-barrier
+    // pattern); the last CTA's thread fences again before the reads
     __syncthreads();
-    if (tid == 0) fw[0] = (atomicAdd(p.ticket, 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
+    if (tid == 0) {
+        __threadfence();
+        fw[0] = (atomicAdd(p.ticket, 1u) == (uint32_t)(G - 1)) ? 1u : 0u;
+        if (fw[0]) __threadfence();
+    }
     __syncthreads();
     if (!fw[0]) return;
-    __threadfence();
     // the last CTA: each round's rule against that round's flags
     for (uint32_t i = tid; i < K * nvw; i += blockDim.x) {
         const uint32_t s = i / nvw, wd = i - s * nvw;
