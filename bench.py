@@ -41,8 +41,8 @@ WORKLOAD = ("training-process image: 1,000 buffers, log-normal 256 B-512 MB, 40 
 # kernels, from single-launch ncu captures of the current kernels: one
 # 1.3M-record trace, the 260M-record launch over 200 distinct traces, and the
 # device -> device copy's bytes over its algorithmic read + write bytes
-TRAFFIC_ONE_TRACE = 10490880 + 512              # profiles/validate_b_one_trace_1p3M.md
-TRAFFIC_260M = 2.085962e9 + 32.033536e6         # profiles/validate_b_distinct_traces_260M.md
+TRAFFIC_ONE_TRACE = 10490880 + 0                # profiles/validate_b_one_trace_1p3M.md
+TRAFFIC_260M = 2.085153e9 + 32.298240e6         # profiles/validate_b_distinct_traces_260M.md
 TRAFFIC_COPY_D2D_RATIO = (1879184896 + 1832464128) / (2 * 1879019520.0)  # copy_main_d2d_2GB.md
 
 
