@@ -6,7 +6,8 @@ them, and regenerates them piece by piece to compare).
     on the memory the first checkpoint left): 1,000 buffers, 40 GB, 200
     kernels, 4 MB pieces, copier quota image/100 per round, 2 GB staging,
     DMA host legs for pieces >= 256 KiB, the copier on its own stream -- the
-    benchmark's step.  Traces are shortened to 16,384 records per kernel
+    benchmark's step -- with each kernel's validation at once and deferred
+    (16 rounds per launch).  Traces are shortened to 16,384 records per kernel
     (only the strays, which are loads here, can change a decision, and the
     oracle's validation is a linear scan).
   * large on-demand restore (Sec. 6): 10,000 buffers, log-normal 4 KB -
@@ -83,7 +84,8 @@ def dma_host_legs():
     phos.host_copy_config(phos.HOST_COPY_DEFAULT)
 
 
-def test_training_image_full_size(dma_host_legs):
+@pytest.mark.parametrize("rounds", ["concurrent", "deferred"])
+def test_training_image_full_size(dma_host_legs, rounds):
     s = torch.cuda.current_stream().cuda_stream
     cfg = wl.training(scale=1.0, n_kernels=200)
     rng, lay = cfg["rng"], cfg["layout"]
@@ -104,7 +106,7 @@ def test_training_image_full_size(dma_host_legs):
     t0 = time.time()
     exp = P.cow_checkpoint(proc, kernels, staging_bytes, chunk, quota)
     t_orc = time.time() - t0
-    got = dp.run_cow(image, quota, chunk, staging, staging_bytes, rounds="concurrent")
+    got = dp.run_cow(image, quota, chunk, staging, staging_bytes, rounds=rounds)
     torch.cuda.synchronize()
     assert exp.misspec is None and got["stats"]["misspec_round"] == -1
     assert got["kernels_run"] == exp.kernels_run
@@ -118,7 +120,7 @@ def test_training_image_full_size(dma_host_legs):
 
     # soft recopy on the memory the CoW checkpoint left
     exp2 = P.recopy_checkpoint(proc, kernels, chunk, quota)
-    got2 = dp.run_recopy(image, quota, chunk, rounds="concurrent")
+    got2 = dp.run_recopy(image, quota, chunk, rounds=rounds)
     torch.cuda.synchronize()
     assert got2["kernels_run"] == exp2.kernels_run
     assert got2["dirty"].tolist() == exp2.dirty and len(exp2.dirty) > 0
@@ -127,8 +129,8 @@ def test_training_image_full_size(dma_host_legs):
         assert got2["stats"][key] == exp2.stats[key]
     assert image_mismatches(exp2.image, image.numpy(), lay, dp.img_off) == []
     assert arena_mismatches(proc.mem, arena) == []
-    print("training 40 GB: oracle CoW run %.1f s, %d CoW copies, %d copier pieces, "
-          "%d dirty" % (t_orc, len(exp.cow_log), len(exp.copier_log), len(exp2.dirty)))
+    print("training 40 GB (%s): oracle CoW run %.1f s, %d CoW copies, %d copier pieces, "
+          "%d dirty" % (rounds, t_orc, len(exp.cow_log), len(exp.copier_log), len(exp2.dirty)))
 
 
 def test_large_restore_full_buffer_count(dma_host_legs):
