@@ -930,9 +930,11 @@ RESTORE = ("large on-demand restore: 10,000 buffers log-normal 4 KB-2 GB, %.0f G
            "before each kernel) vs stop-the-world restore then the same replay")
 
 
-def stall_split(stalls, od):
+def stall_split(stalls, od, link_gbs=None):
     """Stall percentiles of the kernels that waited for on-demand copies and
-    of those that did not."""
+    of those that did not; with link_gbs, the time the link needs for the
+    on-demand bytes alone (p50 / p99 over the kernels that have any), the
+    floor under their stalls."""
     od = np.asarray(od)[:len(stalls)]
     out = {}
     for name, m in (("with_ondemand", od > 0), ("without_ondemand", od == 0)):
@@ -941,6 +943,14 @@ def stall_split(stalls, od):
                       "p99_ms": float(np.percentile(x, 99)),
                       "ondemand_mb_mean": float(od[m].mean() / 1e6)} if len(x) else
                      {"kernels": 0})
+        if len(x) and name == "with_ondemand":
+            out[name]["ondemand_mb_p99"] = float(np.percentile(od[m], 99) / 1e6)
+            if link_gbs:
+                out[name]["link_floor_ms_p50"] = float(np.percentile(od[m], 50) / link_gbs / 1e6)
+                out[name]["link_floor_ms_p99"] = float(np.percentile(od[m], 99) / link_gbs / 1e6)
+    if link_gbs and len(od):
+        # over every kernel, as the stall percentiles of the arm are
+        out["all_kernels_link_floor_ms_p99"] = float(np.percentile(od, 99) / link_gbs / 1e6)
     return out
 
 
@@ -1090,7 +1100,7 @@ def restore_line(args, world):
             "concurrent": {"total_ms": total, "first_kernel_ms": first_ms,
                            "stall_p50_ms": float(np.percentile(stalls, 50)),
                            "stall_p99_ms": float(np.percentile(stalls, 99)),
-                           "stall_split": stall_split(stalls, st["od_per_kernel"]),
+                           "stall_split": stall_split(stalls, st["od_per_kernel"], pcie_h2d),
                            "kernels_during_restore": during,
                            "ondemand_bytes": st["ondemand_bytes"],
                            "copier_bytes": st["copier_bytes"],
@@ -1101,7 +1111,7 @@ def restore_line(args, world):
                 "window_bytes": quota, "total_ms": win[0], "first_kernel_ms": win[1],
                 "stall_p50_ms": float(np.percentile(win[2], 50)),
                 "stall_p99_ms": float(np.percentile(win[2], 99)),
-                "stall_split": stall_split(win[2], win[3]["od_per_kernel"])},
+                "stall_split": stall_split(win[2], win[3]["od_per_kernel"], pcie_h2d)},
             "lockstep": {"total_ms": lock[0], "first_kernel_ms": lock[1],
                          "stall_p50_ms": float(np.percentile(lock[2], 50)),
                          "stall_p99_ms": float(np.percentile(lock[2], 99))},
