@@ -380,7 +380,8 @@ def iterative_recopy(proc, kernels, chunk, quota, max_passes, stop_bytes):
                   kernels_run=k, stats=stats)
 
 
-def concurrent_restore(proc, image, kernels, chunk, quota, copier_stream=False):
+def concurrent_restore(proc, image, kernels, chunk, quota, copier_stream=False,
+                       ondemand_first=False):
     """Section 6 soft on-demand concurrent restore, then the rest of the
     kernels.  proc.mem holds whatever was there before (not restored).
 
@@ -391,7 +392,14 @@ def concurrent_restore(proc, image, kernels, chunk, quota, copier_stream=False):
     round are then in place, since the copier's pieces land in order).  A
     buffer counts as restored for the mis-speculation rule once it is
     present and its last copier piece is at or below the latest round
-    waited for; bytes and the final memory are the same either way."""
+    waited for; bytes and the final memory are the same either way.
+
+    ondemand_first (with copier_stream): a round fetches its kernel's
+    missing buffers first and advances the copier after, so the copier
+    never moves a buffer the round's kernel needs (those are present by
+    then) and the kernel never waits for its own round's pieces.  The
+    session ends when every buffer is present at the start of a round."""
+    assert copier_stream or not ondemand_first
     n = proc.n
     present = [False] * n
     last = [-1] * n                       # round of the copier's last piece of buffer i
@@ -416,9 +424,13 @@ def concurrent_restore(proc, image, kernels, chunk, quota, copier_stream=False):
         return False
 
     while k < len(kernels):
-        cp.advance(quota, move, k, skip=lambda i: present[i])
-        if all(present):
-            break
+        if ondemand_first:
+            if all(present):
+                break
+        else:
+            cp.advance(quota, move, k, skip=lambda i: present[i])
+            if all(present):
+                break
         kern = kernels[k]
         perm = proc.speculate(kern)
         if copier_stream:
@@ -435,6 +447,8 @@ def concurrent_restore(proc, image, kernels, chunk, quota, copier_stream=False):
                 cp.state[i] = DONE
                 present[i] = True
         before = [present[i] and (not copier_stream or last[i] <= waited) for i in range(n)]
+        if ondemand_first:
+            cp.advance(quota, move, k, skip=lambda i: present[i])
         proc.run_kernel(k, kern)
         res = proc.validate(perm, kern)
         k += 1

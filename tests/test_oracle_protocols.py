@@ -276,6 +276,92 @@ def test_restore_copier_stream_wait_covers_earlier_pieces():
     assert ok_lock and ok_stream
 
 
+def _odf_restore(seed, chunk=4096, quota=8192, kernels=None, K=40, sizes=None):
+    """The same restore with the copier on its own stream, in both round
+    orders: the copier's move before the round's on-demand copies (the
+    default) and after them (ondemand_first)."""
+    rng, lay, proc = make_proc(seed, sizes=sizes)
+    image = P.stw_checkpoint(proc)
+    ks = kernels(rng, lay) if kernels else seq(rng, lay, K)
+    ref = P.Process(VA0, lay.off, lay.size, np.zeros(lay.arena_bytes, np.uint8), seed)
+    P.stw_restore(ref, image)
+    for j, k in enumerate(ks):
+        ref.run_kernel(j, k)
+    mask = np.zeros(lay.arena_bytes, bool)
+    for o, sz in zip(lay.off, lay.size):
+        mask[int(o):int(o) + int(sz)] = True
+    out = []
+    for odf in (False, True):
+        cur = P.Process(VA0, lay.off, lay.size, np.full(lay.arena_bytes, 0xA5, np.uint8),
+                        seed)
+        res = P.concurrent_restore(cur, image, ks, chunk, quota, copier_stream=True,
+                                   ondemand_first=odf)
+        out.append((res, np.array_equal(cur.mem[mask], ref.mem[mask])))
+    return ks, lay, out
+
+
+@pytest.mark.parametrize("seed,chunk,quota", [(60, 4096, 8192), (61, 256, 1024),
+                                              (62, 1 << 16, 1 << 17)])
+def test_restore_ondemand_first_equals_stw_restore_plus_replay(seed, chunk, quota):
+    """Sec. 6 correctness in the on-demand-first round order: the final
+    memory is the stop-the-world restore followed by the replay, as in the
+    default order; every byte is restored once (copier + on-demand = the
+    image's buffers), and the copier never moves a buffer the same round's
+    kernel is speculated to access."""
+    ks, lay, out = _odf_restore(seed, chunk=chunk, quota=quota)
+    (a, ok_a), (b, ok_b) = out
+    assert ok_a and ok_b and a.misspec is None and b.misspec is None
+    total = int(sum(int(s) for s in lay.size))
+    assert b.stats["ondemand_bytes"] + b.stats["copier_bytes"] == total
+    rng = np.random.default_rng(0)
+    proc = P.Process(VA0, lay.off, lay.size, np.zeros(lay.arena_bytes, np.uint8), seed)
+    for r, i, off, ln, _ in b.copier_log:
+        if r < b.kernels_during:
+            assert proc.speculate(ks[r])[i] == 0, (r, i)
+    # in the default order the copier does move buffers of its round's kernel
+    assert any(r < a.kernels_during and proc.speculate(ks[r])[i] != 0
+               for r, i, off, ln, _ in a.copier_log)
+
+
+def test_restore_ondemand_first_scenario():
+    """Five 8 KiB buffers, two 4 KiB pieces per round.  K0 needs B0: in the
+    default order the copier's round 0 moves B0 and K0 waits for those
+    pieces; on demand first, K0 fetches B0 itself and the copier's round 0
+    moves B1.  K1 needs B1: present either way (copied in round 0 or 1).
+    K2 needs B2 and B3: B3 on demand in both orders; B2 the copier moved in
+    round 2 of the default order (K2 waits for it), in round 1 on demand
+    first."""
+    sizes = np.full(5, 8192, np.uint64)
+
+    def ks(rng, lay):
+        return [kernel(rng, lay, [0], [0]), kernel(rng, lay, [1], [1]),
+                kernel(rng, lay, [2, 3], [3])]
+    kk, lay, out = _odf_restore(74, sizes=sizes, chunk=4096, quota=8192, kernels=ks)
+    (a, ok_a), (b, ok_b) = out
+    assert ok_a and ok_b and a.misspec is None and b.misspec is None
+    assert [(e[0], e[1]) for e in a.ondemand] == [(2, 3)]
+    assert [(e[0], e[1]) for e in a.copier_log][:6] == [(0, 0), (0, 0), (1, 1), (1, 1),
+                                                      (2, 2), (2, 2)]
+    assert [(e[0], e[1]) for e in b.ondemand] == [(0, 0), (2, 3)]
+    assert [(e[0], e[1]) for e in b.copier_log][:4] == [(0, 1), (0, 1), (1, 2), (1, 2)]
+
+
+def test_restore_ondemand_first_misspeculation_rolls_back():
+    """A stray load of a buffer not yet restored rolls back in the
+    on-demand-first order too, at the same round."""
+    sizes = np.full(8, 8192, np.uint64)
+
+    def ks(rng, lay):
+        k1 = kernel(rng, lay, [0], [1])
+        k1.trace[3] = np.uint64(int(lay.base(VA0)[7]) + 64)     # stray load
+        k1.labels[3] = wl.CLS_OTHER
+        return [kernel(rng, lay, [0], [0]), k1, kernel(rng, lay, [2], [3])]
+    kk, lay, out = _odf_restore(71, sizes=sizes, chunk=4096, quota=4096, kernels=ks)
+    (a, ok_a), (b, ok_b) = out
+    assert a.misspec == 1 and b.misspec == 1
+    assert ok_a and ok_b
+
+
 def test_restore_planted_mistake_is_caught(monkeypatch):
     """An oracle that skips on-demand copies reads stale data, and the
     read-dependent mutator makes the final memory differ."""

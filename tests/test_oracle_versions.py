@@ -184,9 +184,11 @@ def test_recopy_versions_equals_bytes(seed, chunk, quota, strays, passes):
     assert same_mem(b, v)
 
 
-@pytest.mark.parametrize("seed,chunk,quota,stream,strays", [
-    (8, 4096, 8192, False, False), (9, 256, 2048, True, False), (10, 4096, 8192, True, True)])
-def test_restore_versions_equals_bytes(seed, chunk, quota, stream, strays):
+@pytest.mark.parametrize("seed,chunk,quota,stream,strays,odf", [
+    (8, 4096, 8192, False, False, False), (9, 256, 2048, True, False, False),
+    (10, 4096, 8192, True, True, False), (11, 4096, 8192, True, False, True),
+    (12, 256, 2048, True, True, True)])
+def test_restore_versions_equals_bytes(seed, chunk, quota, stream, strays, odf):
     rng, lay = world(seed)
     ks = kernels(rng, lay, 30, strays)
     if strays:                                  # a stray load of a buffer not yet restored
@@ -197,8 +199,10 @@ def test_restore_versions_equals_bytes(seed, chunk, quota, stream, strays):
     v = V.VersionProcess(VA0, lay.off, lay.size, KEY, seed, arena_bytes=lay.arena_bytes)
     image_b = core.words(b.image_bytes, img_key, 0)
     image_v = V.VArray(v.image_bytes, V.Words(img_key), 0)
-    rb = P.concurrent_restore(b, image_b, ks, chunk, quota, copier_stream=stream)
-    rv = P.concurrent_restore(v, image_v, ks, chunk, quota, copier_stream=stream)
+    rb = P.concurrent_restore(b, image_b, ks, chunk, quota, copier_stream=stream,
+                              ondemand_first=odf)
+    rv = P.concurrent_restore(v, image_v, ks, chunk, quota, copier_stream=stream,
+                              ondemand_first=odf)
     assert rb.ondemand == rv.ondemand and rb.copier_log == rv.copier_log
     assert rb.misspec == rv.misspec and rb.kernels_during == rv.kernels_during
     assert rb.stats == rv.stats
