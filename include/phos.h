@@ -528,6 +528,18 @@ enum { PHOS_CKPT_DEVICE = 0x400 };
  * in one CTA's shared memory, is validated at once (after the queued
  * rounds). */
 enum { PHOS_CKPT_DEFER = 0x800 };
+/* Restore flags only, with PHOS_CKPT_CONCURRENT (Sec. 6 leaves the order
+ * within a round open): each round fetches its kernel's missing buffers
+ * first and moves the copier after -- per round: before_kernel(perm), then
+ * advance(quota, &done), the kernel, after_kernel -- so the copier never
+ * moves a buffer that round's kernel needs, the kernel never waits for its
+ * own round's copier pieces, and the copier's pieces start after the
+ * round's on-demand copies (which then have the link to themselves).
+ * advance is allowed only there, once per round; done = 1 means every
+ * buffer is restored (or a mis-speculation has been seen): the round's
+ * kernel and after_kernel still belong to the session, and the caller
+ * starts no further round.  EINVAL without PHOS_CKPT_CONCURRENT. */
+enum { PHOS_RESTORE_ONDEMAND_FIRST = 0x1000 };
 
 typedef struct {
     uint32_t mode;           /* PHOS_CKPT_COW (Sec. 4.2) or PHOS_CKPT_RECOPY

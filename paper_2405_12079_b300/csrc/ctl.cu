@@ -691,6 +691,7 @@ struct phos_ckpt {
     uint64_t release_batch = 0, waited_release = 0;
     DevRounds *dr = nullptr;      // PHOS_CKPT_DEVICE: decisions on the device
     ~phos_ckpt() {
+        ss.pend.clear();      // an ended session validates nothing more
         ss.sync_streams();
         delete dr;
     }
@@ -1142,6 +1143,9 @@ struct phos_restore {
     uint64_t copier_bytes = 0, ondemand_bytes = 0;
     int64_t misspec = -1;
     bool in_kernel = false;
+    // PHOS_RESTORE_ONDEMAND_FIRST: a round's copier move comes after its
+    // on-demand copies (advance inside the round, once)
+    bool odf = false, advanced = false;
     uint64_t waited = 0;     // concurrent: latest copier batch the caller's stream waited for
     // integrity check: manifest digests, per-buffer accumulators and tile
     // counters, the lowest corrupt buffer (mapped host word)
@@ -1160,6 +1164,7 @@ struct phos_restore {
     DevRounds *dr = nullptr;      // PHOS_CKPT_DEVICE: decisions on the device
 
     ~phos_restore() {
+        ss.pend.clear();      // an ended session validates nothing more
         ss.sync_streams();
         delete dr;
         if (d_vacc) cudaFree(d_vacc);
@@ -1187,8 +1192,11 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
         return fail(PHOS_EINVAL, "restore_begin: image smaller than %llu bytes",
                     (unsigned long long)t->image_bytes);
     if (d->flags & ~(uint32_t)(PHOS_CKPT_NO_SYNC | PHOS_CKPT_CONCURRENT | PHOS_CKPT_DEVICE |
-                               PHOS_CKPT_DEFER))
+                               PHOS_CKPT_DEFER | PHOS_RESTORE_ONDEMAND_FIRST))
         return fail(PHOS_EINVAL, "restore_begin: flags %#x", d->flags);
+    if ((d->flags & PHOS_RESTORE_ONDEMAND_FIRST) && !(d->flags & PHOS_CKPT_CONCURRENT))
+        return fail(PHOS_EINVAL, "restore_begin: PHOS_RESTORE_ONDEMAND_FIRST needs "
+                                 "PHOS_CKPT_CONCURRENT");
     if ((d->flags & PHOS_CKPT_DEFER) && (d->flags & PHOS_CKPT_DEVICE))
         return fail(PHOS_EINVAL, "restore_begin: PHOS_CKPT_DEFER goes without PHOS_CKPT_DEVICE");
     if ((d->flags & PHOS_CKPT_DEVICE) && ((d->flags & PHOS_CKPT_CONCURRENT) || d->d_manifest))
@@ -1212,6 +1220,7 @@ extern "C" phos_status phos_restore_begin(const phos_table_t *t, const phos_rest
     r->image = d->image;
     r->image_bytes = d->image_bytes;
     r->d_present = d->d_present;
+    r->odf = (d->flags & PHOS_RESTORE_ONDEMAND_FIRST) != 0;
     if (d->d_manifest) {
         cudaError_t ce;
         const size_t nn = std::max(t->n, 1u);
@@ -1336,6 +1345,19 @@ static phos_status restore_rollback(phos_restore *R, int64_t k) {
 
 extern "C" phos_status phos_restore_advance(phos_restore_t *R, uint64_t quota, int *done) {
     if (!R) return fail(PHOS_EINVAL, "restore_advance: NULL session");
+    if (R->odf) {
+        // inside the round, after its on-demand copies, once
+        if (!R->in_kernel || R->advanced)
+            return fail(PHOS_EINVAL, "restore_advance: with PHOS_RESTORE_ONDEMAND_FIRST, once "
+                                     "per round, after before_kernel");
+        R->advanced = true;
+        // a mis-speculation the device has seen: the round's kernel and
+        // after_kernel still follow (they roll back); no more copier moves
+        const bool seen = R->ss.nosync && R->misspec < 0 && R->ss.flag() >= 0;
+        phos_status r = (seen || R->all_present()) ? PHOS_OK : restore_advance(R, quota);
+        if (done) *done = (seen || R->all_present()) ? 1 : 0;
+        return r;
+    }
     if (R->in_kernel) return fail(PHOS_EINVAL, "restore_advance: inside a kernel round");
     phos_status r = PHOS_OK;
     if (R->ss.nosync && R->misspec < 0 && R->ss.flag() >= 0) {
@@ -1358,6 +1380,7 @@ extern "C" phos_status phos_restore_advance(phos_restore_t *R, uint64_t quota, i
 extern "C" phos_status phos_restore_before_kernel(phos_restore_t *R, const uint8_t *perm) {
     if (!R) return fail(PHOS_EINVAL, "restore_before_kernel: NULL session");
     if (R->in_kernel) return fail(PHOS_EINVAL, "restore_before_kernel: after_kernel missing");
+    R->advanced = false;
     Session &S = R->ss;
     const phos_table *t = S.t;
     phos_status r = S.stage_perm(perm);

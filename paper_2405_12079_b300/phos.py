@@ -106,6 +106,7 @@ CKPT_NO_SYNC = 0x100
 CKPT_CONCURRENT = 0x200
 CKPT_DEVICE = 0x400
 CKPT_DEFER = 0x800
+RESTORE_ONDEMAND_FIRST = 0x1000
 
 
 REQ_CHECKPOINT, REQ_RESTORE = 1, 2

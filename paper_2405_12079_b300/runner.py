@@ -89,12 +89,14 @@ class DeviceProcess:
     def _flags(rounds):
         """rounds: "sync" (wait for each validation), "nosync" (rule on the
         device), "concurrent" (nosync, copier on its own stream), "deferred"
-        (concurrent, up to 16 rounds validated per launch) or "device"
-        (every round's decisions on the device, perms from device
-        speculation)."""
+        (concurrent, up to 16 rounds validated per launch), "odfirst"
+        (restore only: concurrent, each round's on-demand copies before its
+        copier move) or "device" (every round's decisions on the device,
+        perms from device speculation)."""
         return {"sync": 0, "nosync": phos.CKPT_NO_SYNC,
                 "concurrent": phos.CKPT_CONCURRENT,
                 "deferred": phos.CKPT_CONCURRENT | phos.CKPT_DEFER,
+                "odfirst": phos.CKPT_CONCURRENT | phos.RESTORE_ONDEMAND_FIRST,
                 "device": phos.CKPT_DEVICE}[rounds]
 
     def device_perms(self):
@@ -223,15 +225,17 @@ class DeviceProcess:
                          d_manifest.data_ptr() if d_manifest is not None else None)
         k = 0
         K = len(self.kernels)
+        odf = rounds == "odfirst"
         while k < K:
-            if r.advance(quota):
+            if not odf and r.advance(quota):
                 break
             pk = self.kernels[k]
             self._before(r, k, device)
+            done = odf and r.advance(quota)      # after the round's on-demand copies
             self.run_kernel(k)
             misspec = r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1
-            if misspec:
+            if misspec or done:
                 break
         r.finish()
         if r.stats()["misspec_round"] >= 0:  # rolled back: replay what ran

@@ -205,7 +205,8 @@ def check_restore(w, quota, chunk, rounds="sync"):
     w.arena.fill_(0xA5)
     cur = w.oracle_proc(np.full(w.lay.arena_bytes, 0xA5, np.uint8))
     exp = P.concurrent_restore(cur, image, w.kernels, chunk, quota,
-                               copier_stream=rounds in ("concurrent", "deferred"))
+                               copier_stream=rounds in ("concurrent", "deferred", "odfirst"),
+                               ondemand_first=rounds == "odfirst")
     present = torch.zeros(4 * ((w.lay.n + 31) // 32), dtype=torch.uint8, device="cuda")
     got = w.dp.run_restore(img, quota, chunk, present, rounds=rounds)
     torch.cuda.synchronize()
@@ -226,7 +227,7 @@ def check_restore(w, quota, chunk, rounds="sync"):
 
 
 @pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "concurrent-window",
-                                    "deferred", "device"])
+                                    "deferred", "odfirst", "odfirst-window", "device"])
 def test_large_restore_scaled(rounds):
     """Large-restore shape at small scale: 10,000 buffers, layer-local
     read/write sets, background bulk restore plus on-demand copies.  With a
@@ -238,7 +239,7 @@ def test_large_restore_scaled(rounds):
         return wl.make_restore_kernels(rng, lay, va0, cfg["n_kernels"], cfg["n_rec"])
     w = World(cfg["layout"], cfg["seed"], mk)
     quota = a256(w.dp.image_bytes / 300)
-    if rounds == "concurrent-window":
+    if rounds.endswith("-window"):
         phos.copier_window(2 * quota)
     try:
         got, exp = check_restore(w, quota, 64 * 1024, rounds.split("-")[0])
@@ -247,7 +248,8 @@ def test_large_restore_scaled(rounds):
     assert len(exp.ondemand) > 0
 
 
-@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "deferred", "device"])
+@pytest.mark.parametrize("rounds", ["sync", "nosync", "concurrent", "deferred", "odfirst",
+                                    "device"])
 def test_restore_stray_load_rolls_back(rounds):
     cfg = wl.training(scale=0.0005, seed=wl.SEED0 + 22, n_kernels=40)
 
@@ -403,3 +405,31 @@ def test_deferred_rounds_with_ragged_traces(mode):
     w = World(cfg["layout"], wl.SEED0 + 43, mk)
     quota = a256(w.dp.image_bytes / 50)
     check_ckpt(w, mode, quota, 32 * 1024, staging_bytes=1 << 20, rounds="deferred")
+
+
+def test_restore_ondemand_first_rejects_misuse():
+    """PHOS_RESTORE_ONDEMAND_FIRST needs the copier stream, and its advance
+    comes once per round, after before_kernel."""
+    cfg = wl.training(scale=0.0005, seed=wl.SEED0 + 23, n_kernels=4)
+
+    def mk(rng, lay, va0):
+        return wl.make_training_kernels(rng, lay, va0, 4, cfg["n_rec"])
+    w = World(cfg["layout"], cfg["seed"], mk)
+    img = torch.zeros(w.dp.image_bytes, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(phos.PhosError):
+        phos.Restore(w.dp.table, img.data_ptr(), img.numel(), 4096, 4, None, s,
+                     phos.RESTORE_ONDEMAND_FIRST)
+    r = phos.Restore(w.dp.table, img.data_ptr(), img.numel(), 4096, 4, None, s,
+                     phos.CKPT_CONCURRENT | phos.RESTORE_ONDEMAND_FIRST)
+    with pytest.raises(phos.PhosError):
+        r.advance(1 << 20)                       # not inside a round
+    pk = w.dp.kernels[0]
+    r.before_kernel(pk.speculate(w.dp.table, w.dp.perm))
+    r.advance(1 << 20)
+    with pytest.raises(phos.PhosError):
+        r.advance(1 << 20)                       # twice in one round
+    w.dp.run_kernel(0)
+    r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
+    r.finish()
+    r.close()
