@@ -1018,11 +1018,13 @@ def restore_line(args, world):
         prev = a
         k, first = 0, None
         K = len(dp.kernels)
+        odf = rounds == "odfirst"
         while k < K:
-            if r.advance(quota):
+            if not odf and r.advance(quota):
                 break
             pk = dp.kernels[k]
             r.before_kernel(pk.speculate(dp.table, dp.perm))
+            done = odf and r.advance(quota)      # after the round's on-demand copies
             e1 = torch.cuda.Event(enable_timing=True)
             e1.record()
             evs.append((prev, e1))
@@ -1031,7 +1033,7 @@ def restore_line(args, world):
             prev.record()
             mis = r.after_kernel(pk.d_trace.data_ptr(), pk.n_rec)
             k += 1
-            if mis:
+            if mis or done:
                 break
         r.finish()
         if r.stats()["misspec_round"] >= 0:     # rolled back: replay what ran
@@ -1082,6 +1084,8 @@ def restore_line(args, world):
     phos.copier_window(quota)
     try:
         win = concurrent("concurrent")
+        # the same window, each round's on-demand copies before its copier move
+        odw = concurrent("odfirst")
     finally:
         phos.copier_window(0)
     clk = Clocks(dev)
@@ -1112,6 +1116,12 @@ def restore_line(args, world):
                 "stall_p50_ms": float(np.percentile(win[2], 50)),
                 "stall_p99_ms": float(np.percentile(win[2], 99)),
                 "stall_split": stall_split(win[2], win[3]["od_per_kernel"], pcie_h2d)},
+            "concurrent_ondemand_first_window": {
+                "window_bytes": quota, "total_ms": odw[0], "first_kernel_ms": odw[1],
+                "stall_p50_ms": float(np.percentile(odw[2], 50)),
+                "stall_p99_ms": float(np.percentile(odw[2], 99)),
+                "stall_split": stall_split(odw[2], odw[3]["od_per_kernel"], pcie_h2d),
+                "ondemand_bytes": odw[3]["ondemand_bytes"]},
             "lockstep": {"total_ms": lock[0], "first_kernel_ms": lock[1],
                          "stall_p50_ms": float(np.percentile(lock[2], 50)),
                          "stall_p99_ms": float(np.percentile(lock[2], 99))},
@@ -1128,7 +1138,8 @@ def restore_line(args, world):
             "first_kernel_speedup": stw_restore_ms / max(first_ms, 1e-6),
             "verified": {"final_memory_equals_stw_restore_plus_replay":
                          bool(torch.equal(dig_stw, dig_cc)) and bool(torch.equal(dig_stw, lock[5]))
-                         and bool(torch.equal(dig_stw, win[5]))},
+                         and bool(torch.equal(dig_stw, win[5]))
+                         and bool(torch.equal(dig_stw, odw[5]))},
             "gpu_launches": launches, "clocks": clocks}
     return line
 
