@@ -673,7 +673,10 @@ phos_status phos_image_manifest(const phos_table_t *t, const void *image, uint64
 phos_status phos_restore_begin(const phos_table_t *t, const phos_restore_desc_t *d,
                                phos_stream_t stream, phos_restore_t **out);
 /* Background bulk restore of up to quota bytes, skipping present buffers
- * and never writing one.  *done = 1 once every buffer is present. */
+ * and never writing one.  *done = 1 once every buffer is present.  Called
+ * between rounds (before before_kernel), or, with
+ * PHOS_RESTORE_ONDEMAND_FIRST, once inside each round after
+ * before_kernel (EINVAL otherwise). */
 phos_status phos_restore_advance(phos_restore_t *r, uint64_t quota, int *done);
 /* Copy the not-yet-restored bytes of every buffer with perm != 0 before
  * the kernel runs (the kernel waits for them). */
