@@ -39,10 +39,12 @@ WORKLOAD = ("training-process image: 1,000 buffers, log-normal 256 B-512 MB, 40 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the roofline
 # kernels, from single-launch ncu captures of the current kernels: one
-# 1.3M-record trace, the 260M-record launch over 200 distinct traces, and the
-# device -> device copy's bytes over its algorithmic read + write bytes
+# 1.3M-record trace, the 260M-record launch over 200 distinct traces, one
+# deferred launch of 16 rounds of 1.3M records, and the device -> device
+# copy's bytes over its algorithmic read + write bytes
 TRAFFIC_ONE_TRACE = 10490880 + 0                # profiles/validate_b_one_trace_1p3M.md
 TRAFFIC_260M = 2.085153e9 + 32.298240e6         # profiles/validate_b_distinct_traces_260M.md
+TRAFFIC_ROUNDS_16 = 166490624 + 3168256        # profiles/validate_rounds_16x1p3M.md
 TRAFFIC_COPY_D2D_RATIO = (1879184896 + 1832464128) / (2 * 1879019520.0)  # copy_main_d2d_2GB.md
 
 
@@ -478,6 +480,28 @@ def run_gpu(args, rank, world):
     val_recs = sum(p.n_rec for p in dp.kernels)
     val_launch_us = 1e3 * val_ms / len(dp.kernels)
     val_gbs = val_recs * 8.125 / (val_ms * 1e6)
+    # the same 200 traces as a deferred no-sync recopy session validates
+    # them: launches of 16 kernel rounds, each round against its own perms
+    # (8 B read per record; no bitmap is written)
+    rs_bytes, rs_max = phos.harness_rounds_scratch(dp.table)
+    r_per = min(16, rs_max)
+    r_scr = torch.zeros(max(rs_bytes, 256), dtype=torch.uint8, device="cuda")
+    r_flags = torch.ones(max(lay.n, 1), dtype=torch.uint8, device="cuda")
+    r_dirty = torch.zeros(max(lay.n, 1), dtype=torch.uint8, device="cuda")
+    r_acc = torch.from_numpy(np.array([0, 0, 0, 0, 2**64 - 1, 0, 0, 0], np.uint64)
+                             .view(np.uint8).copy()).cuda()
+    r_flag = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    r_rounds = [(p.d_trace.data_ptr(), p.n_rec, pm.data_ptr(), r_flags.data_ptr(), k)
+                for k, (p, pm) in enumerate(zip(dp.kernels, perms))]
+
+    def val_deferred():
+        for j in range(0, len(r_rounds), r_per):
+            phos.harness_validate_rounds(dp.table, r_rounds[j:j + r_per], 4, 1,
+                                         r_dirty.data_ptr(), r_acc.data_ptr(),
+                                         r_flag.data_ptr(), stw.data_ptr(), r_scr.data_ptr(), s)
+    def_launches = -(-len(r_rounds) // max(r_per, 1))
+    def_ms = ev_ms(val_deferred) if r_per else float("nan")
+    def_gbs = val_recs * 8.0 / (def_ms * 1e6)
     # L2 flush before each single-launch repetition: a 256 MB write, then a
     # 256 MB read of another buffer, so that L2 holds clean lines of neither
     # input (a write alone leaves ~126 MB of dirty lines that the timed
@@ -602,6 +626,16 @@ def run_gpu(args, rank, world):
                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                  "traffic_source": "profiles/validate_b_one_trace_1p3M.md (ncu DRAM bytes of "
                                    "one 1.3M-record launch), scaled by records"},
+                {"kernel": "k_validate_rounds, the same traces in deferred launches of %d "
+                           "kernel rounds (%d launches; each round its own speculated perms, "
+                           "recopy rule; 8 B read per record)" % (r_per, def_launches),
+                 "bound": "hbm", "achieved": def_gbs, "peak": hbm, "unit": "GB/s",
+                 "frac": def_gbs / hbm, "traffic": TRAFFIC_ROUNDS_16 * r_per / 16.0,
+                 "traffic_source": "profiles/validate_rounds_16x1p3M.md (ncu DRAM bytes of one "
+                                   "16-round launch), scaled by rounds",
+                 "accesses_per_s": val_recs / (def_ms * 1e-3),
+                 "avg_launch_us": 1e3 * def_ms / def_launches,
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
                 {"kernel": "k_validate_b, one launch over 50 traces (65M records, union of "
                            "their speculated sets, L2 flushed)",
                  "bound": "hbm", "achieved": cat_gbs, "peak": hbm, "unit": "GB/s",

@@ -89,6 +89,43 @@ phos_status phos_harness_fill(uint64_t ptr, uint64_t len, uint64_t key, phos_str
 phos_status phos_harness_table_rebind(phos_table_t *t, int device, int *old_device);
 phos_status phos_harness_table_scratch(const phos_table_t *t, uint64_t *val_bytes);
 
+/* Deferred validation of several kernel rounds in one launch, as a no-sync
+ * checkpoint or restore session with PHOS_CKPT_DEFER runs it (Sec. 4.1
+ * "Runtime validation" with the response of Sec. 4.3, 4.2 or 6), exposed so
+ * that tests and benchmarks can reach the launch directly.  Round i checks
+ * d_trace[0, n_rec) (device, 16-byte aligned; access width access_bytes)
+ * against its own d_perm (device, n bytes) and answers with its own d_flags
+ * (device, n bytes):
+ *   rule 1 (recopy):  every store victim b with d_flags[b] != 0 gets
+ *                     d_dirty[b] = 1;
+ *   rule 2 (CoW):     a store victim b with d_flags[b] == 0 makes the round a
+ *                     mis-speculation;
+ *   rule 3 (restore): any victim b with d_flags[b] == 0 does.
+ * d_acc (device u64[8]): d_acc[3] += the violations of all rounds; if
+ * (int64)d_acc[4] < 0 and some round mis-speculated, d_acc[4] and *d_flag
+ * (device-accessible int64, e.g. mapped pinned memory) become the `round`
+ * of the first such round in the array's order.  d_status as for
+ * phos_validate.  d_scratch: phos_harness_rounds_scratch bytes of device
+ * memory, zeroed once by the caller; each launch leaves it zeroed, and
+ * launches that overlap on the GPU must not share it.  k <= 16; EINVAL if
+ * the table is too large for k rounds in one launch. */
+typedef struct {
+    const uint64_t *d_trace;
+    uint64_t n_rec;
+    const uint8_t *d_perm;
+    const uint8_t *d_flags;
+    int64_t round;
+} phos_harness_round_t;
+phos_status phos_harness_validate_rounds(const phos_table_t *t, const phos_harness_round_t *rounds,
+                                         uint32_t k, uint32_t access_bytes, uint32_t rule,
+                                         uint8_t *d_dirty, uint64_t *d_acc, int64_t *d_flag,
+                                         uint32_t *d_status, void *d_scratch,
+                                         phos_stream_t stream);
+/* Bytes of the scratch above for the table (any k), and the most rounds one
+ * launch takes for it (0: the table is too large for deferred validation). */
+phos_status phos_harness_rounds_scratch(const phos_table_t *t, uint64_t *bytes,
+                                        uint32_t *max_rounds);
+
 #ifdef __cplusplus
 }
 #endif

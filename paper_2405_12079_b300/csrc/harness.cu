@@ -275,3 +275,40 @@ extern "C" phos_status phos_harness_table_scratch(const phos_table_t *t, uint64_
     *val_bytes = T->val_scratch.bytes;
     return PHOS_OK;
 }
+
+// Deferred validation launch, as sessions run it (see phos_harness.h).
+extern "C" phos_status phos_harness_validate_rounds(const phos_table_t *t,
+                                                   const phos_harness_round_t *rounds, uint32_t k,
+                                                   uint32_t access_bytes, uint32_t rule,
+                                                   uint8_t *d_dirty, uint64_t *d_acc,
+                                                   int64_t *d_flag, uint32_t *d_status,
+                                                   void *d_scratch, phos_stream_t stream) {
+    if (!t || (k && !rounds) || !d_acc || !d_flag || !d_scratch)
+        return fail(PHOS_EINVAL, "harness_validate_rounds: NULL argument");
+    if (rule < 1 || rule > 3) return fail(PHOS_EINVAL, "harness_validate_rounds: rule %u", rule);
+    if (rule == 1 && !d_dirty) return fail(PHOS_EINVAL, "harness_validate_rounds: NULL d_dirty");
+    if (access_bytes == 0) return fail(PHOS_EINVAL, "harness_validate_rounds: access_bytes is 0");
+    const uint32_t cap = rounds_cap(t->n, t->device);
+    if (k > cap)
+        return fail(PHOS_EINVAL, "harness_validate_rounds: %u rounds, at most %u for %u buffers", k,
+                    cap, t->n);
+    std::vector<RoundSeg> seg(k);
+    for (uint32_t i = 0; i < k; ++i) {
+        const phos_harness_round_t &R = rounds[i];
+        if (R.n_rec && (!R.d_trace || ((uintptr_t)R.d_trace & 15)))
+            return fail(PHOS_EINVAL, "harness_validate_rounds: round %u trace NULL or unaligned", i);
+        if (t->n && (!R.d_perm || !R.d_flags))
+            return fail(PHOS_EINVAL, "harness_validate_rounds: round %u perm or flags NULL", i);
+        seg[i] = RoundSeg{R.d_trace, R.n_rec, R.d_perm, R.d_flags, R.round};
+    }
+    return validate_rounds(t, seg.data(), k, access_bytes, rule, d_dirty, d_acc, d_flag, d_status,
+                           d_scratch, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" phos_status phos_harness_rounds_scratch(const phos_table_t *t, uint64_t *bytes,
+                                                  uint32_t *max_rounds) {
+    if (!t || !bytes) return fail(PHOS_EINVAL, "harness_rounds_scratch: NULL argument");
+    *bytes = rounds_scratch_bytes(t->n, kMaxRounds);
+    if (max_rounds) *max_rounds = rounds_cap(t->n, t->device);
+    return PHOS_OK;
+}

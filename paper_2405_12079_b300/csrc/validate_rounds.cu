@@ -14,6 +14,16 @@
 //     j, then the records are checked word by word against those leaders
 //     (batch_words).  Batches never straddle two rounds; they are taken
 //     grid-stride, CTA-minor, over the rounds' concatenated batch ranges.
+//   * Rounds with long traces (the training step's 1.3M records per kernel)
+//     take 32-word batches (1,024 records) instead: an 8-word batch pays its
+//     leader searches on a quarter of the records, ~1.45x the cost per
+//     record.  The host picks the width with the plain validation's cost
+//     model, words x (W + 6) / W for the busiest warp.  16 rounds of 1.3M
+//     records: 76.6 -> 62.7 us per launch.  What the streaming kernel adds on
+//     top measured slower here: an L2 prefetch of each warp's next batch
+//     raised DRAM reads to 1.29x the records' bytes (67.6 us), loading the
+//     next batch's leader records ahead cost 67.6 us, and batches from a
+//     shared counter instead of grid-stride changed nothing (62.8 us).
 //   * Every round's permissions and victim bitmaps sit in shared memory
 //     next to the table, so a batch only switches pointers.
 //   * One last-CTA epilogue per launch applies each round's rule: recopy
@@ -31,8 +41,8 @@
 namespace phos {
 
 constexpr uint32_t kRoundThreads = 512;
-constexpr uint32_t kRoundW = 8;   // words per batch
-constexpr uint64_t kRoundBatch = 32ull * kRoundW;
+constexpr uint32_t kRoundWShort = 8;   // words per batch: short rounds
+constexpr uint32_t kRoundWLong = 32;   // long rounds
 
 struct RoundsParams {
     TableDev tab;
@@ -40,6 +50,7 @@ struct RoundsParams {
     uint32_t nvw;                   // victim words per round
     uint32_t k;                     // rounds in this launch
     uint32_t rule;                  // 1 recopy, 2 CoW, 3 restore (see ProtoRule)
+    uint32_t W;                     // words per batch: kRoundWShort or kRoundWLong
     const uint64_t *trace[kMaxRounds];
     const uint8_t *perm[kMaxRounds];
     const uint8_t *flags[kMaxRounds];
@@ -55,15 +66,15 @@ struct RoundsParams {
     uint32_t *ticket;               // zero between calls
 };
 
-static size_t rounds_fixed_smem() {
+static size_t rounds_fixed_smem(uint32_t W) {
     const uint32_t nw = kRoundThreads / 32;
-    return sizeof(Lead) * kRoundW * nw + 4ull * kRoundW * nw + 128;
+    return sizeof(Lead) * W * nw + 4ull * W * nw + 128;
 }
 
 // Each round's permissions sit at a 16-byte aligned stride in shared memory.
-static size_t rounds_smem(uint32_t n, uint32_t k, bool table) {
+static size_t rounds_smem(uint32_t n, uint32_t k, bool table, uint32_t W) {
     const uint32_t nvw = std::max((n + 31) / 32, 1u);
-    return rounds_fixed_smem() + (table ? 16ull * n : 0) + (uint64_t)k * align_up(n, 16) +
+    return rounds_fixed_smem(W) + (table ? 16ull * n : 0) + (uint64_t)k * align_up(n, 16) +
            8ull * k * nvw;
 }
 
@@ -73,11 +84,12 @@ __global__ void __launch_bounds__(kRoundThreads, 2)
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
-    const uint32_t n = p.tab.n, nvw = p.nvw, K = p.k;
-    Lead *leads = reinterpret_cast<Lead *>(smem);                  // [nwarps][kRoundW]
-    uint8_t *cur = smem + sizeof(Lead) * kRoundW * nwarps;
-    uint32_t *words = reinterpret_cast<uint32_t *>(cur);           // [nwarps][kRoundW], unread
-    cur += 4ull * kRoundW * nwarps;
+    const uint32_t n = p.tab.n, nvw = p.nvw, K = p.k, W = p.W;
+    const uint64_t brec = 32ull * W;                               // records per batch
+    Lead *leads = reinterpret_cast<Lead *>(smem);                  // [nwarps][W]
+    uint8_t *cur = smem + sizeof(Lead) * W * nwarps;
+    uint32_t *words = reinterpret_cast<uint32_t *>(cur);           // [nwarps][W], unread
+    cur += 4ull * W * nwarps;
     unsigned long long *red = reinterpret_cast<unsigned long long *>(cur);
     volatile uint32_t *fw = reinterpret_cast<volatile uint32_t *>(cur + 8);  // last, hit[K]
     cur += 128;
@@ -128,17 +140,18 @@ __global__ void __launch_bounds__(kRoundThreads, 2)
 
     const uint64_t G = gridDim.x, c = blockIdx.x, TW = G * nwarps;
     const uint64_t total = p.bstart[K];
-    Lead *mine = leads + kRoundW * warp;
+    Lead *mine = leads + W * warp;
     Acc acc;
+    // a warp's batches ascend, so the round index only moves forward
+    uint32_t s = 0;
     for (uint64_t b = (uint64_t)warp * G + c; b < total; b += TW) {
-        uint32_t s = 0;
         while (s + 1 < K && p.bstart[s + 1] <= b) ++s;
-        const uint64_t r0 = (b - p.bstart[s]) * kRoundBatch;
-        const uint64_t nb = min(kRoundBatch, p.n_rec[s] - r0);
+        const uint64_t r0 = (b - p.bstart[s]) * brec;
+        const uint64_t nb = min(brec, p.n_rec[s] - r0);
         const uint64_t *recs = p.trace[s] + r0;
         L.perm = perms + (size_t)s * np;
         uint32_t *svr = sv + (size_t)s * 2 * nvw;
-        if (lane < kRoundW)
+        if (lane < W)
             mine[lane] = make_lead(
                 L, lane * 32 < nb ? L.lane_search(recs[lane * 32] & PHOS_REC_ADDR_MASK) : -1,
                 kSmemTable);
@@ -146,12 +159,12 @@ __global__ void __launch_bounds__(kRoundThreads, 2)
         // a full batch two words per step (one 16-byte load per lane:
         // traces are 16-byte aligned and batches start at 256-record
         // boundaries), a partial one word by word
-        if (nb == kRoundBatch)
-            batch_pairs<kSmemTable>(L, recs, kRoundW, lane, mine, words + kRoundW * warp, svr,
-                                    svr + nvw, acc);
+        if (nb == brec)
+            batch_pairs<kSmemTable>(L, recs, W, lane, mine, words + W * warp, svr, svr + nvw,
+                                    acc);
         else
-            batch_words<kSmemTable, false>(L, recs, nb, kRoundW, lane, mine,
-                                           words + kRoundW * warp, svr, svr + nvw, acc);
+            batch_words<kSmemTable, false>(L, recs, nb, W, lane, mine, words + W * warp, svr,
+                                           svr + nvw, acc);
         __syncwarp();
     }
     if (__any_sync(0xffffffffu, acc.bad) && lane == 0) set_status(p.status, PHOS_EINVAL);
@@ -208,12 +221,40 @@ __global__ void __launch_bounds__(kRoundThreads, 2)
     }
 }
 
+// CTAs of a launch over b batches: one warp per batch, two CTAs per SM at
+// most.
+static uint64_t rounds_grid(uint64_t b, uint64_t max_ctas) {
+    const uint64_t warps_per_cta = kRoundThreads / 32;
+    return std::max<uint64_t>(1,
+                              std::min<uint64_t>(max_ctas, (b + warps_per_cta - 1) / warps_per_cta));
+}
+
+// Batch width of a launch: the one whose busiest warp has the least work,
+// counting each batch's leader searches as six words on top of its W words
+// (the plain validation's cost model).  Ties keep the short batches.
+static uint32_t rounds_width(const RoundSeg *seg, uint32_t k, uint64_t max_ctas) {
+    uint32_t best = kRoundWShort;
+    uint64_t best_cost = ~0ull;
+    for (uint32_t W : {kRoundWShort, kRoundWLong}) {
+        const uint64_t brec = 32ull * W;
+        uint64_t b = 0;
+        for (uint32_t i = 0; i < k; ++i) b += (seg[i].n_rec + brec - 1) / brec;
+        const uint64_t warps = rounds_grid(b, max_ctas) * (kRoundThreads / 32);
+        const uint64_t cost = (b + warps - 1) / warps * (W + 6);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = W;
+        }
+    }
+    return best;
+}
+
 uint32_t rounds_cap(uint32_t n, int device) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (optin <= 0) optin = 227 * 1024;
     for (uint32_t k = kMaxRounds; k >= 2; --k)
-        if (rounds_smem(n, k, false) <= (size_t)optin) return k;
+        if (rounds_smem(n, k, false, kRoundWShort) <= (size_t)optin) return k;
     return 0;
 }
 
@@ -234,6 +275,14 @@ phos_status validate_rounds(const phos_table_t *t, const RoundSeg *seg, uint32_t
     p.nvw = std::max((t->n + 31) / 32, 1u);
     p.k = k;
     p.rule = rule;
+    int optin = 0;
+    PHOS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device));
+    if (optin <= 0) optin = 227 * 1024;
+    const uint64_t max_ctas = 2ull * sm_count(t->device);
+    const uint32_t W = rounds_width(seg, k, max_ctas);
+    // the wider batches' leader slots must fit next to the rounds' state
+    p.W = rounds_smem(t->n, k, false, W) <= (size_t)optin ? W : kRoundWShort;
+    const uint64_t brec = 32ull * p.W;
     uint64_t b = 0;
     for (uint32_t i = 0; i < k; ++i) {
         p.trace[i] = seg[i].trace;
@@ -242,7 +291,7 @@ phos_status validate_rounds(const phos_table_t *t, const RoundSeg *seg, uint32_t
         p.round[i] = seg[i].round;
         p.n_rec[i] = seg[i].n_rec;
         p.bstart[i] = b;
-        b += (seg[i].n_rec + kRoundBatch - 1) / kRoundBatch;
+        b += (seg[i].n_rec + brec - 1) / brec;
     }
     for (uint32_t i = k; i < kMaxRounds; ++i) {
         p.trace[i] = nullptr;
@@ -262,14 +311,9 @@ phos_status validate_rounds(const phos_table_t *t, const RoundSeg *seg, uint32_t
     p.cnt = reinterpret_cast<unsigned long long *>(sc);
     p.ticket = reinterpret_cast<uint32_t *>(sc + 8);
     p.vacc = reinterpret_cast<uint32_t *>(sc + 256);
-    int optin = 0;
-    PHOS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, t->device));
-    if (optin <= 0) optin = 227 * 1024;
-    const bool table = rounds_smem(t->n, k, true) <= (size_t)optin;
-    const size_t smem = rounds_smem(t->n, k, table);
-    const uint64_t warps_per_cta = kRoundThreads / 32;
-    const uint64_t G = std::max<uint64_t>(
-        1, std::min<uint64_t>(2ull * sm_count(t->device), (b + warps_per_cta - 1) / warps_per_cta));
+    const bool table = rounds_smem(t->n, k, true, p.W) <= (size_t)optin;
+    const size_t smem = rounds_smem(t->n, k, table, p.W);
+    const uint64_t G = rounds_grid(b, max_ctas);
     if (table) {
         phos_status r = smem_optin_once((const void *)k_validate_rounds<true>);
         if (r) return r;

@@ -241,6 +241,93 @@ def bench_validate_rounds(out, K=64, n_rec=65536):
                                     dirty=dirty)
 
 
+def bench_validate_rounds_launch(out, K=16, reps=7):
+    """Deferred validation of K distinct training-kernel traces (1.3M
+    records each, each round its own speculated perms) in one
+    k_validate_rounds launch (phos_harness_validate_rounds, recopy rule),
+    against K phos_validate launches over the same traces and one
+    phos_validate launch over their concatenation with the union of the
+    perms.  L2 flushed before every repetition (a 256 MB write, then a
+    256 MB read of another buffer)."""
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(n_kernels=K)
+    lay, rng = cfg["layout"], cfg["rng"]
+    t = phos.Table(lay.base(VA0), lay.size)
+    ks = wl.make_training_kernels(rng, lay, VA0, K, 1_300_000, 0.001)
+    perms = []
+    for k in ks:
+        p = np.zeros(lay.n, np.uint8)
+        p[k.reads] = phos.PERM_R
+        p[k.writes] = phos.PERM_RW
+        perms.append(torch.from_numpy(p).cuda())
+    trs = [torch.from_numpy(k.trace.view(np.uint8).copy()).cuda() for k in ks]
+    n1 = len(ks[0].trace)
+    N = n1 * K
+    cat = torch.cat(trs)
+    uperm = torch.stack(perms).max(dim=0).values.contiguous()
+    nvw = (lay.n + 31) // 32
+    bm = torch.empty(((N + 31) // 32) * 4, dtype=torch.uint8, device="cuda")
+    cnt = torch.empty(24, dtype=torch.uint8, device="cuda")
+    vv = torch.empty(8 * nvw, dtype=torch.uint8, device="cuda")
+    st = torch.zeros(4, dtype=torch.uint8, device="cuda")
+    sb, kmax = phos.harness_rounds_scratch(t)
+    scr = torch.zeros(max(sb, 256), dtype=torch.uint8, device="cuda")
+    flags = torch.ones(lay.n, dtype=torch.uint8, device="cuda")
+    dirty = torch.zeros(lay.n, dtype=torch.uint8, device="cuda")
+    acc = torch.from_numpy(np.array([0, 0, 0, 0, 2**64 - 1, 0, 0, 0], np.uint64)
+                           .view(np.uint8).copy()).cuda()
+    flag = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    rounds = [(tr.data_ptr(), n1, pm.data_ptr(), flags.data_ptr(), j)
+              for j, (tr, pm) in enumerate(zip(trs, perms))]
+    flw = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flr = torch.ones(256 << 20, dtype=torch.uint8, device="cuda")
+    fl_acc = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def deferred():
+        phos.harness_validate_rounds(t, rounds[:min(K, kmax)], 4, 1, dirty.data_ptr(),
+                                     acc.data_ptr(), flag.data_ptr(), st.data_ptr(),
+                                     scr.data_ptr(), s)
+
+    def per_round():
+        for tr, pm in zip(trs, perms):
+            phos.validate(t, pm.data_ptr(), tr.data_ptr(), n1, 4, bm.data_ptr(), cnt.data_ptr(),
+                          vv.data_ptr(), vv.data_ptr() + 4 * nvw, None, 0, st.data_ptr(), s)
+
+    def concat():
+        phos.validate(t, uperm.data_ptr(), cat.data_ptr(), N, 4, bm.data_ptr(), cnt.data_ptr(),
+                      vv.data_ptr(), vv.data_ptr() + 4 * nvw, None, 0, st.data_ptr(), s)
+
+    def flushed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            flw.zero_()
+            torch.sum(flr.view(torch.int64), dim=(0,), out=fl_acc[0])
+            torch.cuda._sleep(100_000)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts)), float(np.min(ts))
+
+    import time
+    t_warm = time.time() + 1.5
+    while time.time() < t_warm:
+        concat()
+        torch.cuda.synchronize()
+    for name, fn, launches, bpr in (("deferred_one_launch", deferred, 1, 8.0),
+                                    ("per_round_launches", per_round, K, 8.125),
+                                    ("concat_one_launch", concat, 1, 8.125)):
+        med, best = flushed(fn)
+        out["validate_rounds_" + name] = dict(
+            rounds=K, records=N, launches=launches, ms_median=med, ms_best=best,
+            grec_s=N / med / 1e6, gbs=N * bpr / med / 1e6, bytes_per_record=bpr)
+
+
 def bench_copy_misaligned(gb, out):
     """Device -> device copies of G GB in 4 MB regions whose source is
     offset from the destination's alignment by 0, 1, 2, 4, 8 or 12 bytes."""
@@ -365,8 +452,11 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", default="all",
                     choices=["validate", "validate_distinct", "emit", "copy", "copy_misaligned",
-                             "validate_rounds", "speculate", "all"])
+                             "validate_rounds", "validate_rounds_launch", "speculate",
+                             "all"])
     ap.add_argument("--traces", type=int, default=160)
+    ap.add_argument("--rounds-nrec", type=int, default=65536,
+                    help="validate_rounds: records per kernel round's trace")
     ap.add_argument("--copy-gb", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0, help="validate kernel variant (0 = both)")
     a = ap.parse_args()
@@ -380,7 +470,9 @@ def main():
     if a.kernel == "copy_misaligned":
         bench_copy_misaligned(a.copy_gb, out)
     if a.kernel == "validate_rounds":
-        bench_validate_rounds(out)
+        bench_validate_rounds(out, n_rec=a.rounds_nrec)
+    if a.kernel == "validate_rounds_launch":
+        bench_validate_rounds_launch(out)
     if a.kernel in ("copy", "all"):
         bench_copy(a.copy_gb, out)
     if a.kernel in ("speculate", "all"):

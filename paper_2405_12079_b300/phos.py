@@ -65,6 +65,9 @@ _SIGS = {
     "phos_harness_fill": (_i32, [_u64, _u64, _u64, _vp]),
     "phos_harness_table_rebind": (_i32, [_vp, _i32, _P(_i32)]),
     "phos_harness_table_scratch": (_i32, [_vp, _P(_u64)]),
+    "phos_harness_validate_rounds": (_i32, [_vp, _vp, _u32, _u32, _u32, _vp, _vp, _vp, _vp, _vp,
+                                            _vp]),
+    "phos_harness_rounds_scratch": (_i32, [_vp, _P(_u64), _P(_u32)]),
     "phos_plan_create": (_i32, [_vp, _u32, _P(_vp)]),
     "phos_plan_launch": (_i32, [_vp, _vp]),
     "phos_plan_set_tile": (_i32, [_vp, _u64]),
@@ -418,6 +421,32 @@ def harness_table_scratch(table):
     b = _u64()
     check(lib().phos_harness_table_scratch(table.handle, _c.byref(b)), "harness_table_scratch")
     return int(b.value)
+
+
+class HarnessRound(_c.Structure):
+    _fields_ = [("d_trace", _vp), ("n_rec", _u64), ("d_perm", _vp), ("d_flags", _vp),
+                ("round", _c.c_int64)]
+
+
+def harness_validate_rounds(table, rounds, access_bytes, rule, d_dirty, d_acc, d_flag, d_status,
+                            d_scratch, stream=None):
+    """phos_harness_validate_rounds over a sequence of (d_trace, n_rec,
+    d_perm, d_flags, round) tuples (device pointers as integers)."""
+    arr = (HarnessRound * max(len(rounds), 1))()
+    for i, (tr, nr, pm, fl, rd) in enumerate(rounds):
+        arr[i] = HarnessRound(tr, nr, pm, fl, rd)
+    return check(lib().phos_harness_validate_rounds(table.handle, _c.cast(arr, _vp), len(rounds),
+                                                    access_bytes, rule, d_dirty, d_acc, d_flag,
+                                                    d_status, d_scratch, stream),
+                 "harness_validate_rounds")
+
+
+def harness_rounds_scratch(table):
+    """(scratch bytes, most rounds per launch) of deferred validation."""
+    b, k = _u64(), _u32()
+    check(lib().phos_harness_rounds_scratch(table.handle, _c.byref(b), _c.byref(k)),
+          "harness_rounds_scratch")
+    return int(b.value), int(k.value)
 
 
 def _stats_dict(st):

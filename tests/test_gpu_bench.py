@@ -34,6 +34,8 @@ def test_training_line_contract():
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert k in r
     assert line["cpu_baseline"]["kind"] == "oracle"
+    rows = {r["kernel"].split(",")[0]: r for r in line["rooflines"][1:]}
+    assert rows["k_validate_rounds"]["frac"] > 0
     assert set(line["e2e"]) >= {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert "all_cores" in line["cpu_baseline"]["loops"]
     # the batched, serving and restore forms, measured in the same run

@@ -317,6 +317,29 @@ def test_native_driver_equals_oracle(mode, rounds):
     assert w.live_equal(proc)
 
 
+@pytest.mark.parametrize("mode", ["cow", "recopy"])
+def test_deferred_long_traces(mode):
+    """Deferred validation of kernel rounds with long, ragged traces
+    (300K-600K records: the launch takes 32-word batches and prefetches)
+    inside recopy (stray stores: dirty marks by the device rule) and CoW
+    sessions: dirty set or CoW list, copier pieces, image and live memory
+    equal the oracle's."""
+    cfg = wl.training(scale=0.002, seed=wl.SEED0 + 50, n_kernels=24)
+
+    def mk(rng, lay, va0):
+        ks = []
+        for _ in range(24):
+            ks += wl.make_training_kernels(rng, lay, va0, 1, int(rng.integers(300_000, 600_000)),
+                                           0.001, 0.3 if mode == "recopy" else 0.0)
+        return ks
+    w = World(cfg["layout"], cfg["seed"], mk)
+    quota = a256(w.dp.image_bytes / 30)
+    got, exp = check_ckpt(w, mode, quota, 64 * 1024, staging_bytes=4 << 20, rounds="deferred")
+    assert exp.kernels_run == 24
+    if mode == "recopy":
+        assert got["stats"]["violations"] > 0 and len(exp.dirty) > 0
+
+
 @pytest.mark.parametrize("budget", [0, 1 << 20], ids=["no-staging", "staging-1MiB"])
 def test_device_rounds_cow_staging_pressure(budget):
     """Device-decided CoW rounds with little or no staging: the device's
