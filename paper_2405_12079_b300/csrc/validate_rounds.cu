@@ -22,8 +22,9 @@
 //     records: 76.6 -> 62.7 us per launch.  What the streaming kernel adds on
 //     top measured slower here: an L2 prefetch of each warp's next batch
 //     raised DRAM reads to 1.29x the records' bytes (67.6 us), loading the
-//     next batch's leader records ahead cost 67.6 us, and batches from a
-//     shared counter instead of grid-stride changed nothing (62.8 us).
+//     next batch's leader records ahead cost 67.6 us, one record stream
+//     across the warp's batches 63.5 us, and batches from a shared counter
+//     instead of grid-stride changed nothing (62.8 us).
 //   * Every round's permissions and victim bitmaps sit in shared memory
 //     next to the table, so a batch only switches pointers.
 //   * One last-CTA epilogue per launch applies each round's rule: recopy
