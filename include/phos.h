@@ -31,6 +31,12 @@
  *     address) or device memory; pageable host memory is rejected.
  *   - Calls that use the same table handle and run concurrently on
  *     different streams race on the handle's scratch; order them.
+ *   - Device work goes to the calling thread's current CUDA device, which
+ *     must be the device that was current when the handle was created (a
+ *     table records it).  Only phos_validate_noalloc checks this
+ *     (PHOS_EINVAL).  The server is the exception: its own thread, and
+ *     phos_server_submit and phos_server_app_copy on the caller's thread,
+ *     make the server's device current.
  */
 #ifndef PHOS_H
 #define PHOS_H
