@@ -9,6 +9,10 @@ validate: one launch over K concatenated 1.3M-record training-kernel traces
 copy:     G GB of 4 MB regions device->device, device->pinned host and
           pinned host->device through the copy engine, next to the DMA
           engines (torch copy_) on the same buffers.
+validate_rounds:        native recopy sessions, one validation launch per
+          round against deferred validation (--rounds-nrec records per round).
+validate_rounds_launch: one deferred launch over 16 distinct 1.3M-record
+          traces against 16 plain launches and one over their concatenation.
 Prints one JSON object.  Inputs are larger than L2 unless stated.
 """
 import argparse
