@@ -23,19 +23,30 @@
 namespace phos {
 
 constexpr uint64_t kVTile = 256 * 1024;
-constexpr int kVMaxEnt = 64;
+// Regions per launch: a batch travels as the kernel's parameters, 64
+// regions (2 KB) for the short lists of a restore's sub-batches, 1,000
+// (32 KB, near the 32,764-byte parameter limit) for a whole table, so a
+// table of up to 1,000 buffers is one launch whose tiles spread over the
+// whole grid (with 64 regions per launch a 2 GB manifest took 17 thin
+// launches and 0.65 ms).
+constexpr int kVSmall = 64;
+constexpr int kVLarge = 1000;
 
 struct VEnt {
     uint64_t ptr, len;
     uint32_t tile0, tiles, buf, pad;
 };
 
+template <int N>
 struct VBatch {
-    VEnt e[kVMaxEnt];
+    VEnt e[N];
     uint32_t count, tiles;
 };
+static_assert(sizeof(VBatch<kVLarge>) + 5 * sizeof(void *) <= 32764,
+              "k_verify's parameters exceed the launch limit");
 
-__global__ void __launch_bounds__(512) k_verify(const __grid_constant__ VBatch b,
+template <int N>
+__global__ void __launch_bounds__(512) k_verify(const __grid_constant__ VBatch<N> b,
                                                 unsigned long long *acc, uint32_t *cnt,
                                                 const uint64_t *manifest, uint32_t *status,
                                                 int *bad) {
@@ -43,10 +54,16 @@ __global__ void __launch_bounds__(512) k_verify(const __grid_constant__ VBatch b
     if (threadIdx.x == 0) s_acc = 0;
     __syncthreads();
     for (uint32_t t = blockIdx.x; t < b.tiles; t += gridDim.x) {
-        int q = 0;
-        for (int k = 1; k < (int)b.count; ++k)
-            if (b.e[k].tile0 <= t) q = k;
-        const VEnt &e = b.e[q];
+        // the entry holding tile t: the last one whose first tile is <= t
+        int lo = 0, hi = (int)b.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.e[mid].tile0 <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const VEnt &e = b.e[lo];
         const uint64_t off = (uint64_t)(t - e.tile0) * kVTile;
         const uint64_t end = min(off + kVTile, e.len);
         const unsigned long long part = digest_range(reinterpret_cast<const uint8_t *>(e.ptr),
@@ -83,16 +100,17 @@ __global__ void k_vzero(unsigned long long *p, uint32_t n) {
 
 // Digest regions [ptrs[k], +lens[k]) into acc[bufs[k]] (manifest == NULL),
 // or verify them against manifest[bufs[k]] (see k_verify).
-static phos_status digest_regions(const std::vector<uint64_t> &ptrs,
-                                  const std::vector<uint64_t> &lens,
-                                  const std::vector<uint32_t> &bufs, unsigned long long *acc,
-                                  uint32_t *cnt, const uint64_t *manifest, uint32_t *status,
-                                  int *bad, cudaStream_t s) {
-    for (size_t b0 = 0; b0 < ptrs.size(); b0 += kVMaxEnt) {
-        VBatch b;
+template <int N>
+static phos_status digest_regions_n(const std::vector<uint64_t> &ptrs,
+                                    const std::vector<uint64_t> &lens,
+                                    const std::vector<uint32_t> &bufs, unsigned long long *acc,
+                                    uint32_t *cnt, const uint64_t *manifest, uint32_t *status,
+                                    int *bad, cudaStream_t s) {
+    for (size_t b0 = 0; b0 < ptrs.size(); b0 += N) {
+        VBatch<N> b;
         memset(&b, 0, sizeof b);
         uint32_t tiles = 0;
-        b.count = (uint32_t)std::min<size_t>(kVMaxEnt, ptrs.size() - b0);
+        b.count = (uint32_t)std::min<size_t>(N, ptrs.size() - b0);
         for (uint32_t q = 0; q < b.count; ++q) {
             VEnt &e = b.e[q];
             e.ptr = ptrs[b0 + q];
@@ -104,11 +122,21 @@ static phos_status digest_regions(const std::vector<uint64_t> &ptrs,
         }
         b.tiles = tiles;
         const unsigned grid = (unsigned)std::max<uint32_t>(1, std::min<uint32_t>(tiles, 148 * 4));
-        k_verify<<<grid, 512, 0, s>>>(b, acc, cnt, manifest, status, bad);
+        k_verify<N><<<grid, 512, 0, s>>>(b, acc, cnt, manifest, status, bad);
         count_launch();
         PHOS_CUDA(cudaGetLastError());
     }
     return PHOS_OK;
+}
+
+static phos_status digest_regions(const std::vector<uint64_t> &ptrs,
+                                  const std::vector<uint64_t> &lens,
+                                  const std::vector<uint32_t> &bufs, unsigned long long *acc,
+                                  uint32_t *cnt, const uint64_t *manifest, uint32_t *status,
+                                  int *bad, cudaStream_t s) {
+    if (ptrs.size() <= (size_t)kVSmall)
+        return digest_regions_n<kVSmall>(ptrs, lens, bufs, acc, cnt, manifest, status, bad, s);
+    return digest_regions_n<kVLarge>(ptrs, lens, bufs, acc, cnt, manifest, status, bad, s);
 }
 
 phos_status verify_buffers(const phos_table *t, const std::vector<uint32_t> &bufs,

@@ -13,6 +13,11 @@ validate_rounds:        native recopy sessions, one validation launch per
           round against deferred validation (--rounds-nrec records per round).
 validate_rounds_launch: one deferred launch over 16 distinct 1.3M-record
           traces against 16 plain launches and one over their concatenation.
+protocol_kernels:       the small protocol kernels (device-decided rounds,
+          the rule kernel, image manifest and verified restore) in their
+          sessions.
+image_manifest:         the manifest (digest of every buffer) of a 2 GB
+          device-resident image.
 Prints one JSON object.  Inputs are larger than L2 unless stated.
 """
 import argparse
@@ -332,6 +337,65 @@ def bench_validate_rounds_launch(out, K=16, reps=7):
             grec_s=N / med / 1e6, gbs=N * bpr / med / 1e6, bytes_per_record=bpr)
 
 
+def bench_protocol_kernels(out, K=48, n_rec=65536):
+    """The protocol's small kernels in the sessions that launch them, over
+    the 1,000-buffer training layout at 1/20 scale (2 GB arena), K kernel
+    rounds of n_rec-record traces, quota image/40, 4 MB pieces: a
+    device-decided CoW session (k_dr_* with 64 MB of staging), a no-sync
+    recopy session on the ring validation variant (k_rule after each
+    k_validate), and a verified restore of the CoW image (k_vzero and
+    k_verify building the manifest, k_verify on every restored buffer).
+    """
+    from . import runner
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(scale=0.05, n_kernels=K)
+    rng, lay = cfg["rng"], cfg["layout"]
+    arena = torch.empty(lay.arena_bytes, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(arena.data_ptr(), lay.arena_bytes, cfg["seed"], s)
+    kernels = wl.make_training_kernels(rng, lay, arena.data_ptr(), K, n_rec, 0.001)
+    dp = runner.DeviceProcess(lay, arena, cfg["seed"], kernels)
+    image = torch.empty(dp.image_bytes, dtype=torch.uint8).pin_memory()
+    quota = -(-dp.image_bytes // 40 // 256) * 256
+    stg = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    st = dp.run_cow(image, quota, 4 << 20, stg, stg.numel(), rounds="device")["stats"]
+    out["cow_device_rounds"] = dict(rounds=K, cow_bytes=st["cow_bytes"],
+                                    direct_bytes=st["direct_bytes"])
+    phos.validate_config(1)
+    try:
+        st = dp.run_recopy(torch.empty_like(image).pin_memory(), quota, 4 << 20,
+                           rounds="nosync")["stats"]
+    finally:
+        phos.validate_config(0)
+    out["recopy_nosync_ring"] = dict(rounds=K, dirty=st["dirty"])
+    man = torch.empty(8 * lay.n, dtype=torch.uint8, device="cuda")
+    phos.image_manifest(dp.table, image.data_ptr(), image.numel(), man.data_ptr(), s)
+    phos.harness_fill(arena.data_ptr(), lay.arena_bytes, 12345, s)
+    r = dp.run_restore(image, quota, 4 << 20, rounds="concurrent", d_manifest=man)
+    out["restore_verified"] = dict(rounds=r["kernels_during"],
+                                   ondemand=len(r["ondemand"]), copier=len(r["copier"]))
+
+
+def bench_image_manifest(out, scale=0.05, reps=10):
+    """phos_image_manifest over a device-resident image of the 1,000-buffer
+    training layout (2 GB at scale 0.05): k_vzero, then k_verify digesting
+    every buffer (one HBM read of its bytes), CUDA events, L2 not flushed
+    (the image is 16x L2)."""
+    s = torch.cuda.current_stream().cuda_stream
+    cfg = wl.training(scale=scale, n_kernels=1)
+    lay = cfg["layout"]
+    t = phos.Table(lay.base(VA0), lay.size)
+    nb = t.image_bytes()
+    img = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    phos.harness_fill(img.data_ptr(), nb, 7, s)
+    man = torch.empty(8 * lay.n, dtype=torch.uint8, device="cuda")
+    img_bytes = int(lay.size.astype(np.int64).sum())
+    ms = timeit(lambda: phos.image_manifest(t, img.data_ptr(), nb, man.data_ptr(), s), reps,
+                warm=3)
+    out["image_manifest_device"] = dict(buffers=int(lay.n), bytes=img_bytes, ms=ms,
+                                        gbs=img_bytes / ms / 1e6,
+                                        launches_per_call=1 + (lay.n + 63) // 64)
+
+
 def bench_copy_misaligned(gb, out):
     """Device -> device copies of G GB in 4 MB regions whose source is
     offset from the destination's alignment by 0, 1, 2, 4, 8 or 12 bytes."""
@@ -456,8 +520,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--kernel", default="all",
                     choices=["validate", "validate_distinct", "emit", "copy", "copy_misaligned",
-                             "validate_rounds", "validate_rounds_launch", "speculate",
-                             "all"])
+                             "validate_rounds", "validate_rounds_launch", "protocol_kernels",
+                             "image_manifest", "speculate", "all"])
     ap.add_argument("--traces", type=int, default=160)
     ap.add_argument("--rounds-nrec", type=int, default=65536,
                     help="validate_rounds: records per kernel round's trace")
@@ -477,6 +541,10 @@ def main():
         bench_validate_rounds(out, n_rec=a.rounds_nrec)
     if a.kernel == "validate_rounds_launch":
         bench_validate_rounds_launch(out)
+    if a.kernel == "protocol_kernels":
+        bench_protocol_kernels(out)
+    if a.kernel == "image_manifest":
+        bench_image_manifest(out)
     if a.kernel in ("copy", "all"):
         bench_copy(a.copy_gb, out)
     if a.kernel in ("speculate", "all"):
