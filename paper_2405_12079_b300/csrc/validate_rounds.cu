@@ -19,12 +19,13 @@
 //     leader searches on a quarter of the records, ~1.45x the cost per
 //     record.  The host picks the width with the plain validation's cost
 //     model, words x (W + 6) / W for the busiest warp.  16 rounds of 1.3M
-//     records: 76.6 -> 62.7 us per launch.  What the streaming kernel adds on
-//     top measured slower here: an L2 prefetch of each warp's next batch
-//     raised DRAM reads to 1.29x the records' bytes (67.6 us), loading the
-//     next batch's leader records ahead cost 67.6 us, one record stream
-//     across the warp's batches 63.5 us, and batches from a shared counter
-//     instead of grid-stride changed nothing (62.8 us).
+//     records: 74.5-78.8 -> 60.8-64.2 us per launch (ncu durations).  What
+//     the streaming kernel adds on top measured no faster here (CUDA events,
+//     against 61.4-63.5 us): an L2 prefetch of each warp's next batch raised
+//     DRAM reads to 1.29x the records' bytes (67.6 us), loading the next
+//     batch's leader records ahead cost 67.6 us, one record stream across the
+//     warp's batches 63.5 us, and batches from a shared counter instead of
+//     grid-stride 62.8 us.
 //   * Every round's permissions and victim bitmaps sit in shared memory
 //     next to the table, so a batch only switches pointers.
 //   * One last-CTA epilogue per launch applies each round's rule: recopy
